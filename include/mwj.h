@@ -1,0 +1,165 @@
+/*
+ * mwj.h -- C ABI of the GB300 multiway (3-way) hash join library (libmwj.so).
+ *
+ * The library evaluates, on one CUDA device, the single-step 3-way joins of
+ * "Efficient Multiway Hash Join on Reconfigurable Hardware" (arXiv 1905.13376):
+ *
+ *   linear  R(A,B) |x| S(B,C) |x| T(C,D)   (Section 4, Algorithm 1)
+ *   cyclic  R(A,B) |x| S(B,C) |x| T(C,A)   (Section 5)
+ *
+ * and the cascade of two binary hash joins the paper measures them against
+ * (Section 6.3).  Results follow bag semantics (duplicates are not removed,
+ * Section 1, Example 1) and are exact: counts are 64-bit and wrap modulo 2^64.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All data pointers are DEVICE pointers on the context's device unless a
+ *   comment says otherwise.  The caller owns every input, output and
+ *   workspace buffer; the library never frees or retains caller memory
+ *   beyond the call.
+ * - Relations are column pairs of int32 (structure of arrays).  Columns may
+ *   alias (R, S and T may be the same arrays).  n is limited to
+ *   [0, 2^31 - 1] tuples per relation.
+ * - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *   stream.  Calls are stream-ordered: argument errors are returned
+ *   synchronously; errors detected on the device (an A value outside the
+ *   group-by domain, too few output rows, a bounded wait that ran out) are
+ *   recorded in the context's status word and returned by
+ *   mwj_stream_status().  mwj_cascade_join and calls with shares == NULL
+ *   synchronise `stream` once on the host (they read sizes back).
+ * - The library allocates no device memory inside join calls: all scratch
+ *   comes from the caller's workspace, sized by mwj_workspace_size().
+ * - A context is used by one host thread at a time.
+ */
+#ifndef MWJ_H
+#define MWJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MWJ_OK = 0,
+    MWJ_ERR_INVALID_ARG = 1,   /* NULL pointer, n < 0 or too large, share < 1, bad mode/kind */
+    MWJ_ERR_DOMAIN = 2,        /* GROUP BY A: some a outside [0, a_domain) */
+    MWJ_ERR_CAPACITY = 3,      /* MATERIALIZE: more rows than `capacity`; *n_rows holds the exact count */
+    MWJ_ERR_WORKSPACE = 4,     /* workspace too small for this call */
+    MWJ_ERR_CUDA = 5,          /* a CUDA runtime call failed; see mwj_last_error() */
+    MWJ_ERR_TIMEOUT = 6,       /* a bounded device-side wait reached its iteration limit */
+    MWJ_ERR_CHECK = 7,         /* an internal consistency check failed on the device */
+    MWJ_ERR_UNIMPLEMENTED = 8
+} mwj_status;
+
+typedef enum {
+    MWJ_COUNT = 0,             /* COUNT(*) of the join into *total */
+    MWJ_COUNT_GROUP_BY_A = 1,  /* COUNT(*) GROUP BY A into group_counts[a], plus *total */
+    MWJ_MATERIALIZE = 2        /* the joined tuples into rows, plus *n_rows and *total */
+} mwj_mode;
+
+typedef enum { MWJ_LINEAR = 0, MWJ_CYCLIC = 1 } mwj_kind;
+
+/* One relation: n tuples (x[i], y[i]).  Linear: R = (a,b), S = (b,c),
+ * T = (c,d).  Cyclic: R = (a,b), S = (b,c), T = (c,a).  Device, borrowed,
+ * read-only. */
+typedef struct {
+    const int32_t *x;
+    const int32_t *y;
+    int64_t n;
+} mwj_rel;
+
+/* Bucket counts ("shares") of the top-level hash functions (Sections 4.1,
+ * 5 and the analyses 4.2, 5.2).
+ *   linear: s[0] = number of H(B) buckets of R and S; s[1] = number of g(C)
+ *           buckets of S and T (1 = T's tile stays whole in L2, see
+ *           mwj_join3_linear); s[2] ignored.
+ *   cyclic: s = {H(A), G(B), F(C)} bucket counts; tile (i,j,k) joins
+ *           R_ij, S_jk and T_ki.
+ * Every used entry must be >= 1.  A NULL share pointer asks the library's
+ * cost-model planner to choose. */
+typedef struct {
+    int32_t s[3];
+} mwj_shares;
+
+typedef struct {
+    mwj_mode mode;
+    int64_t *total;          /* device, 1 element, always written (all modes) */
+    int64_t *group_counts;   /* device, a_domain elements, overwritten (GROUP BY A) */
+    int32_t a_domain;        /* GROUP BY A: every a of R must lie in [0, a_domain) */
+    int32_t *rows;           /* device, capacity * arity int32, row-major (MATERIALIZE);
+                                arity 4 (a,b,c,d) linear, 3 (a,b,c) cyclic; order unspecified */
+    int64_t capacity;        /* rows available */
+    int64_t *n_rows;         /* device, 1 element: exact number of result rows (MATERIALIZE) */
+} mwj_out;
+
+typedef struct {
+    int32_t device;          /* CUDA device ordinal, -1 = current device */
+    uint32_t seed;           /* seed of the hash functions (results do not depend on it) */
+    int32_t smem_bytes;      /* shared memory per CTA for tiles, 0 = library default */
+    int32_t load_pct;        /* maximum fill of on-chip hash tables in percent, 0 = default (50) */
+    int64_t spin_limit;      /* iteration cap of bounded device waits, 0 = default */
+} mwj_config;
+
+typedef struct mwj_ctx mwj_ctx;
+
+/* Create a context on cfg->device (or the current device when cfg == NULL or
+ * device == -1).  Allocates the context's device status word.  Returns
+ * MWJ_ERR_CUDA if no usable sm_103 device is present. */
+mwj_status mwj_create(mwj_ctx **ctx, const mwj_config *cfg);
+mwj_status mwj_destroy(mwj_ctx *ctx);
+
+/* Bytes of device workspace a call needs.  kind: MWJ_LINEAR / MWJ_CYCLIC for
+ * mwj_join3_*, or 2 + kind for mwj_cascade_join (the cascade then uses any
+ * extra bytes it is given as room for its intermediate relation). */
+mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
+                              const mwj_shares *shares, mwj_mode mode, size_t *bytes);
+
+/* Linear 3-way join R(A,B) S(B,C) T(C,D) in one step (Algorithm 1, Section 4):
+ * R is partitioned by H(B), S by (H(B), g(C)), T by g(C); each CTA holds one
+ * R bucket as an on-chip hash table while the matching S partition streams
+ * past it and T's bucket tables are probed (in shared memory when
+ * shares.s[1] > 1, in L2 when shares.s[1] == 1).  No intermediate relation
+ * is materialised.  workspace: device, >= mwj_workspace_size(ctx, MWJ_LINEAR, ...). */
+mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
+                            const mwj_shares *shares, const mwj_out *out,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* Cyclic 3-way join R(A,B) S(B,C) T(C,A) in one step (Section 5): tile
+ * (i,j,k) of the share cube holds R_ij (H(a)=i, G(b)=j) and T_ki
+ * (F(c)=k, H(a)=i) on chip while S_jk streams past them.  T's columns are
+ * (c, a). */
+mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
+                            const mwj_shares *shares, const mwj_out *out,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* Cascade of binary hash joins (Section 6.3): I(A,B,C) = R join S is
+ * materialised in the workspace (in chunks when it does not fit), then
+ * I join T gives the same result as the 3-way join.  kind = MWJ_LINEAR or
+ * MWJ_CYCLIC.  Synchronises `stream` on the host to size the chunks. */
+mwj_status mwj_cascade_join(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
+                            const mwj_out *out, void *workspace, size_t ws_bytes,
+                            void *stream);
+
+/* Synchronise `stream`, return the first device-side error recorded since the
+ * previous call (MWJ_OK if none) and clear it. */
+mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream);
+
+/* The shares the planner would choose for these relations (host result in
+ * *shares).  kind = MWJ_LINEAR or MWJ_CYCLIC.  Synchronises `stream`. */
+mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
+                           mwj_mode mode, mwj_shares *shares, void *stream);
+
+/* Human-readable text of the last error on this context (static storage of
+ * the context; valid until the next call). */
+const char *mwj_last_error(mwj_ctx *ctx);
+
+/* Library version string, e.g. "mwj 0.1 sm_103a". */
+const char *mwj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWJ_H */

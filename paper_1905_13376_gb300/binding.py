@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libmwj (include/mwj.h).
+
+The functions ``mwj_*`` mirror the C ABI one to one (argument marshalling
+only).  ``Context`` adds convenience: it takes int32 CUDA tensors, allocates
+outputs and the workspace with torch, and raises ``MwjError`` on a non-OK
+status.  Every step of every join runs in the library's CUDA kernels; there is
+no CPU path, and loading fails loudly when the library cannot be built or
+loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+MWJ_OK = 0
+MWJ_ERR_INVALID_ARG = 1
+MWJ_ERR_DOMAIN = 2
+MWJ_ERR_CAPACITY = 3
+MWJ_ERR_WORKSPACE = 4
+MWJ_ERR_CUDA = 5
+MWJ_ERR_TIMEOUT = 6
+MWJ_ERR_CHECK = 7
+MWJ_ERR_UNIMPLEMENTED = 8
+
+MWJ_COUNT = 0
+MWJ_COUNT_GROUP_BY_A = 1
+MWJ_MATERIALIZE = 2
+
+MWJ_LINEAR = 0
+MWJ_CYCLIC = 1
+
+MODES = {"count": MWJ_COUNT, "group_by_a": MWJ_COUNT_GROUP_BY_A, "rows": MWJ_MATERIALIZE}
+
+
+class mwj_rel(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class mwj_shares(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32 * 3)]
+
+
+class mwj_out(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("total", ctypes.c_void_p),
+                ("group_counts", ctypes.c_void_p), ("a_domain", ctypes.c_int32),
+                ("rows", ctypes.c_void_p), ("capacity", ctypes.c_int64),
+                ("n_rows", ctypes.c_void_p)]
+
+
+class mwj_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("seed", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_int32), ("load_pct", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64)]
+
+
+class MwjError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mwj status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbols and their signatures: (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "mwj_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(mwj_config)]),
+    "mwj_destroy": (ctypes.c_int, [_P]),
+    "mwj_workspace_size": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
+                                          ctypes.POINTER(mwj_shares), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "mwj_join3_linear": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
+                                        ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_join3_cyclic": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
+                                        ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
+                                        ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_stream_status": (ctypes.c_int, [_P, _P]),
+    "mwj_plan_shares": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel, ctypes.c_int,
+                                       ctypes.POINTER(mwj_shares), _P]),
+    "mwj_last_error": (ctypes.c_char_p, [_P]),
+    "mwj_version": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_lib", "libmwj.so")
+
+
+def load():
+    """Load libmwj.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    # mwj_* functions resolve to the library's exports
+    if name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+# ---------------------------------------------------------------------------
+# convenience layer over torch tensors
+# ---------------------------------------------------------------------------
+
+def _rel(pair):
+    import torch
+    x, y = pair
+    assert x.dtype == torch.int32 and y.dtype == torch.int32, "relations are int32 column pairs"
+    assert x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()
+    assert x.numel() == y.numel()
+    return mwj_rel(x.data_ptr(), y.data_ptr(), x.numel())
+
+
+def _shares(s):
+    if s is None:
+        return None
+    v = list(s) + [1] * (3 - len(s))
+    sh = mwj_shares()
+    for i in range(3):
+        sh.s[i] = int(v[i])
+    return ctypes.byref(sh)
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int | None = None, seed: int = 0, load_pct: int = 0,
+                 spin_limit: int = 0):
+        import torch
+        self.lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device)
+        cfg = mwj_config(device, seed & 0xFFFFFFFF, 0, load_pct, spin_limit)
+        h = _P()
+        st = self.lib.mwj_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != MWJ_OK:
+            raise MwjError(st, "mwj_create failed")
+        self.h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mwj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != MWJ_OK:
+            raise MwjError(st, self.lib.mwj_last_error(self.h).decode())
+
+    def workspace(self, nbytes: int):
+        import torch
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def workspace_size(self, kind, R, S, T, shares=None, mode=MWJ_COUNT) -> int:
+        n = ctypes.c_size_t()
+        self._check(self.lib.mwj_workspace_size(self.h, kind, _rel(R), _rel(S), _rel(T),
+                                                _shares(shares), mode, ctypes.byref(n)))
+        return n.value
+
+    def plan_shares(self, kind, R, S, T, mode=MWJ_COUNT, stream=None):
+        sh = mwj_shares()
+        self._check(self.lib.mwj_plan_shares(self.h, kind, _rel(R), _rel(S), _rel(T), mode,
+                                             ctypes.byref(sh), self._stream(stream)))
+        return tuple(sh.s)
+
+    def _stream(self, stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _outputs(self, mode, a_domain, capacity, arity):
+        import torch
+        dev = self.device
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        o = mwj_out()
+        o.mode = mode
+        o.total = total.data_ptr()
+        res = {"total": total}
+        if mode == MWJ_COUNT_GROUP_BY_A:
+            cnt = torch.empty(int(a_domain), dtype=torch.int64, device=dev)
+            o.group_counts = cnt.data_ptr()
+            o.a_domain = int(a_domain)
+            res["counts"] = cnt
+        if mode == MWJ_MATERIALIZE:
+            rows = torch.empty((max(int(capacity), 1), arity), dtype=torch.int32, device=dev)
+            n_rows = torch.zeros(1, dtype=torch.int64, device=dev)
+            o.rows = rows.data_ptr()
+            o.capacity = int(capacity)
+            o.n_rows = n_rows.data_ptr()
+            res["rows"] = rows
+            res["n_rows"] = n_rows
+        return o, res
+
+    def _run(self, fn, kind_ws, R, S, T, mode, shares, a_domain, capacity, arity, stream, sync,
+             extra=()):
+        if isinstance(mode, str):
+            mode = MODES[mode]
+        o, res = self._outputs(mode, a_domain, capacity, arity)
+        nb = self.workspace_size(kind_ws, R, S, T, shares if kind_ws < 2 else None, mode)
+        ws = self.workspace(nb)
+        args = (self.h,) + tuple(extra) + (_rel(R), _rel(S), _rel(T))
+        if kind_ws < 2:
+            args = args + (_shares(shares),)
+        st = fn(*args, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                self._stream(stream))
+        self._check(st)
+        if sync:
+            self._check(self.lib.mwj_stream_status(self.h, self._stream(stream)))
+            if mode == MWJ_MATERIALIZE:
+                n = int(res["n_rows"].item())
+                res["rows"] = res["rows"][:n]
+        return res
+
+    def join3_linear(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
+                     stream=None, sync=True):
+        return self._run(self.lib.mwj_join3_linear, MWJ_LINEAR, R, S, T, mode, shares, a_domain,
+                         capacity, 4, stream, sync)
+
+    def join3_cyclic(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
+                     stream=None, sync=True):
+        return self._run(self.lib.mwj_join3_cyclic, MWJ_CYCLIC, R, S, T, mode, shares, a_domain,
+                         capacity, 3, stream, sync)
+
+    def cascade_join(self, kind, R, S, T, mode="count", a_domain=None, capacity=0, stream=None,
+                     sync=True, workspace_bytes=None):
+        if isinstance(mode, str):
+            mode = MODES[mode]
+        o, res = self._outputs(mode, a_domain, capacity, 4 if kind == MWJ_LINEAR else 3)
+        nb = self.workspace_size(2 + kind, R, S, T, None, mode)
+        if workspace_bytes is not None:
+            nb = max(nb, int(workspace_bytes))
+        ws = self.workspace(nb)
+        st = self.lib.mwj_cascade_join(self.h, kind, _rel(R), _rel(S), _rel(T), ctypes.byref(o),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       self._stream(stream))
+        self._check(st)
+        if sync:
+            self._check(self.lib.mwj_stream_status(self.h, self._stream(stream)))
+            if mode == MWJ_MATERIALIZE:
+                res["rows"] = res["rows"][:int(res["n_rows"].item())]
+        return res

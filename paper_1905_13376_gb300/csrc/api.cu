@@ -1,0 +1,349 @@
+// api.cu -- the C ABI of include/mwj.h: argument checks, workspace layout and
+// the order of the kernels of each join.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "api_internal.h"
+#include "linear.h"
+#include "tables.h"
+
+using namespace mwj;
+
+namespace mwj {
+
+const char *status_text(int s) {
+    switch (s) {
+        case MWJ_OK: return "ok";
+        case MWJ_ERR_INVALID_ARG: return "invalid argument";
+        case MWJ_ERR_DOMAIN: return "a value of A lies outside [0, a_domain)";
+        case MWJ_ERR_CAPACITY: return "more result rows than the output capacity";
+        case MWJ_ERR_WORKSPACE: return "workspace too small";
+        case MWJ_ERR_CUDA: return "CUDA error";
+        case MWJ_ERR_TIMEOUT: return "a bounded device wait ran out";
+        case MWJ_ERR_CHECK: return "device consistency check failed";
+        case MWJ_ERR_UNIMPLEMENTED: return "not implemented";
+        default: return "unknown status";
+    }
+}
+
+mwj_status fail(mwj_ctx *ctx, mwj_status s, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+mwj_status cuda_fail(mwj_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, MWJ_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool rel_ok(const mwj_rel &r) {
+    if (r.n < 0 || r.n > 0x7FFFFFFFll) return false;
+    if (r.n > 0 && (!r.x || !r.y)) return false;
+    return true;
+}
+
+uint32_t pow2_at_least(uint64_t v) {
+    uint32_t p = 1;
+    while (p < v && p < (1u << 30)) p <<= 1;
+    return p;
+}
+
+}  // namespace mwj
+
+// ---------------------------------------------------------------------------
+// linear join: workspace layout
+// ---------------------------------------------------------------------------
+namespace {
+
+struct LinPlan {
+    uint32_t I, J, JT;
+    bool rows;
+};
+
+// bucket count of T's tables: small buckets so that each is aggregated in
+// one CTA's shared memory; equal to J when S is split by g(C) as well.
+uint32_t t_buckets(int64_t nT, uint32_t J) {
+    if (J > 1) return J;
+    uint64_t want = (uint64_t)(nT + 2047) / 2048;
+    uint32_t p = pow2_at_least(want ? want : 1);
+    return p > kMaxBuckets ? kMaxBuckets : p;
+}
+
+struct LinLayout {
+    uint2 *Rp; uint32_t *offR;
+    uint2 *Sp; uint32_t *offS;
+    uint32_t *Tk; uint2 *Tp; uint32_t *offT;
+    uint64_t *img; uint32_t *capT; uint32_t *startT; int32_t *dlist;
+    void *pscratch; size_t pscratch_bytes;
+    unsigned long long *rowcount, *base; void *sscratch;
+};
+
+size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S,
+                  const mwj_rel &T, int num_sms, LinLayout &L) {
+    L.Rp = A.take<uint2>(R.n + 2);
+    L.offR = A.take<uint32_t>(p.I + 1);
+    L.Sp = A.take<uint2>(S.n + 2);
+    L.offS = A.take<uint32_t>((size_t)p.I * p.J + 1);
+    if (p.rows) {
+        L.Tk = nullptr;
+        L.Tp = A.take<uint2>(T.n + 2);
+    } else {
+        L.Tk = A.take<uint32_t>(T.n + 4);
+        L.Tp = nullptr;
+    }
+    L.offT = A.take<uint32_t>(p.JT + 1);
+    L.img = A.take<uint64_t>(2 * (size_t)T.n + 4);
+    L.capT = A.take<uint32_t>(p.JT + 1);
+    if (p.rows) {
+        L.startT = A.take<uint32_t>(2 * (size_t)T.n + 4);
+        L.dlist = A.take<int32_t>(T.n + 4);
+        L.rowcount = A.take<unsigned long long>(p.I + 1);
+        L.base = A.take<unsigned long long>(p.I + 2);
+        L.sscratch = A.take<char>(scan_scratch_bytes(p.I + 1));
+    } else {
+        L.startT = nullptr;
+        L.dlist = nullptr;
+        L.rowcount = L.base = nullptr;
+        L.sscratch = nullptr;
+    }
+    size_t ps = part_scratch_bytes(R.n, p.I, num_sms);
+    size_t ps2 = part_scratch_bytes(S.n, p.I * p.J, num_sms);
+    size_t ps3 = part_scratch_bytes(T.n, p.JT, num_sms);
+    if (ps2 > ps) ps = ps2;
+    if (ps3 > ps) ps = ps3;
+    L.pscratch = A.take<char>(ps);
+    L.pscratch_bytes = ps;
+    return A.used;
+}
+
+}  // namespace
+
+namespace mwj {
+
+mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                               mwj_shares *sh) {
+    (void)S;
+    (void)T;
+    // R bucket tables of 2^13 slots hold up to ~4K distinct B values; aim for
+    // ~2K tuples of R per bucket and at least two CTAs per SM.
+    uint64_t want = (uint64_t)(R.n + 2047) / 2048;
+    uint64_t minb = (uint64_t)ctx->dev.num_sms * 2;
+    if (want < minb) want = minb;
+    uint32_t I = pow2_at_least(want);
+    if (I > 16384) I = 16384;
+    sh->s[0] = (int32_t)I;
+    sh->s[1] = 1;
+    sh->s[2] = 1;
+    return MWJ_OK;
+}
+
+mwj_status lin_check_shares(mwj_ctx *ctx, const mwj_shares *sh, uint32_t *I, uint32_t *J) {
+    if (sh->s[0] < 1 || sh->s[1] < 1) return fail(ctx, MWJ_ERR_INVALID_ARG, "shares must be >= 1");
+    uint64_t P = (uint64_t)sh->s[0] * (uint64_t)sh->s[1];
+    if ((uint64_t)sh->s[0] > kMaxBuckets || P > kMaxBuckets)
+        return fail(ctx, MWJ_ERR_INVALID_ARG, "linear shares: I*J must be <= %u", kMaxBuckets);
+    *I = (uint32_t)sh->s[0];
+    *J = (uint32_t)sh->s[1];
+    return MWJ_OK;
+}
+
+}  // namespace mwj
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *mwj_version(void) { return "mwj 0.1 sm_103a"; }
+
+mwj_status mwj_create(mwj_ctx **out, const mwj_config *cfg) {
+    if (!out) return MWJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    mwj_ctx *ctx = new mwj_ctx();
+    std::memset(ctx->err, 0, sizeof(ctx->err));
+    mwj_config c{};
+    if (cfg) c = *cfg;
+    int dev = c.device;
+    cudaError_t e;
+    if (dev < 0) {
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
+    }
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
+    ctx->dev.device = dev;
+    cudaDeviceGetAttribute(&ctx->dev.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&ctx->dev.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&ctx->dev.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&ctx->dev.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+    ctx->seed = c.seed;
+    ctx->seeds = make_seeds(c.seed);
+    ctx->smem_bytes = c.smem_bytes;
+    ctx->load_pct = c.load_pct > 0 ? c.load_pct : 50;
+    ctx->spin_limit = c.spin_limit > 0 ? c.spin_limit : (1ll << 26);
+    e = cudaMalloc(&ctx->status, sizeof(DevStatus));
+    if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
+    e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
+    if (e != cudaSuccess) { cudaFree(ctx->status); delete ctx; return MWJ_ERR_CUDA; }
+    *out = ctx;
+    return MWJ_OK;
+}
+
+mwj_status mwj_destroy(mwj_ctx *ctx) {
+    if (!ctx) return MWJ_ERR_INVALID_ARG;
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+    return MWJ_OK;
+}
+
+const char *mwj_last_error(mwj_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream) {
+    if (!ctx) return MWJ_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    DevStatus h{};
+    e = cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (h.code != 0) {
+        DevStatus z{};
+        cudaMemcpy(ctx->status, &z, sizeof(z), cudaMemcpyHostToDevice);
+        return fail(ctx, (mwj_status)h.code, "%s (detail %lld)", status_text(h.code),
+                    (long long)h.aux);
+    }
+    return MWJ_OK;
+}
+
+mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
+                              const mwj_shares *shares, mwj_mode mode, size_t *bytes) {
+    if (!ctx || !bytes) return MWJ_ERR_INVALID_ARG;
+    if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
+    if (mode < MWJ_COUNT || mode > MWJ_MATERIALIZE) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad mode");
+    mwj_shares sh;
+    if (kind == MWJ_LINEAR) {
+        if (shares) sh = *shares; else plan_linear_default(ctx, R, S, T, &sh);
+        LinPlan p;
+        mwj_status s = lin_check_shares(ctx, &sh, &p.I, &p.J);
+        if (s != MWJ_OK) return s;
+        p.JT = t_buckets(T.n, p.J);
+        p.rows = (mode == MWJ_MATERIALIZE);
+        Arena A(nullptr, 0);
+        LinLayout L;
+        *bytes = lin_layout(A, p, R, S, T, ctx->dev.num_sms, L);
+        return MWJ_OK;
+    }
+    if (kind == MWJ_CYCLIC) return cyc_workspace(ctx, R, S, T, shares, mode, bytes);
+    if (kind == 2 + MWJ_LINEAR || kind == 2 + MWJ_CYCLIC)
+        return cascade_workspace(ctx, kind - 2, R, S, T, mode, bytes);
+    return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind %d", kind);
+}
+
+mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
+                            const mwj_shares *shares, const mwj_out *out, void *workspace,
+                            size_t ws_bytes, void *stream) {
+    if (!ctx || !out) return MWJ_ERR_INVALID_ARG;
+    if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
+    mwj_status s = check_out(ctx, out, 4);
+    if (s != MWJ_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    mwj_shares sh;
+    if (shares) sh = *shares; else plan_linear_default(ctx, R, S, T, &sh);
+    LinPlan p;
+    s = lin_check_shares(ctx, &sh, &p.I, &p.J);
+    if (s != MWJ_OK) return s;
+    p.JT = t_buckets(T.n, p.J);
+    p.rows = (out->mode == MWJ_MATERIALIZE);
+    Arena A(workspace, ws_bytes);
+    LinLayout L;
+    lin_layout(A, p, R, S, T, ctx->dev.num_sms, L);
+    if (A.overflow || !workspace)
+        return fail(ctx, MWJ_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, A.used);
+
+    const Seeds &sd = ctx->seeds;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(out->total, 0, sizeof(int64_t), st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "memset total");
+    if (out->mode == MWJ_COUNT_GROUP_BY_A &&
+        (e = cudaMemsetAsync(out->group_counts, 0, sizeof(int64_t) * (size_t)out->a_domain, st)) !=
+            cudaSuccess)
+        return cuda_fail(ctx, e, "memset group_counts");
+    // Algorithm 1, steps 1-3: T by g(C), S by (H(B), g(C)), R by H(B)
+    PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
+    e = part_run(T.x, T.y, T.n, pt, p.rows ? PAY_PAIR : PAY_X, p.rows ? (void *)L.Tp : (void *)L.Tk,
+                 L.offT, L.pscratch, L.pscratch_bytes, ctx->dev.num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");
+    PartSpec ps{0, sd.B, p.I, p.J > 1 ? 1 : -1, sd.C, p.J};
+    e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
+                 ctx->dev.num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
+    PartSpec pr{1, sd.B, p.I, -1, 0, 1};
+    e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
+                 ctx->dev.num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
+    // T's bucket tables
+    e = tables_build(L.Tk, L.Tp, L.offT, p.JT, sd.slot2, L.img, L.capT, L.startT, L.dlist,
+                     ctx->dev.num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "T tables");
+
+    LinArgs g{};
+    g.Rp = L.Rp; g.offR = L.offR; g.Sp = L.Sp; g.offS = L.offS; g.I = p.I; g.JS = p.J;
+    g.t = TImg{L.img, L.offT, L.capT, L.startT, L.dlist, p.JT, sd.C, sd.slot2};
+    g.cap_log2 = 13;
+    g.seed_slot = sd.slot;
+    g.a_domain = out->a_domain;
+    g.cnt = (unsigned long long *)out->group_counts;
+    g.total = (unsigned long long *)out->total;
+    g.rowcount = L.rowcount;
+    g.st = ctx->status;
+    int mode = out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0;
+    if ((e = lin_agg_launch(g, mode, st)) != cudaSuccess) return cuda_fail(ctx, e, "linear probe");
+    if (p.rows) {
+        e = scan_excl_u64((const uint64_t *)L.rowcount, (uint64_t *)L.base, p.I, true, L.sscratch, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "row scan");
+        e = lin_rows_launch(g, L.base, out->rows, out->capacity, (long long *)out->n_rows, 16384, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "linear rows");
+    }
+    return MWJ_OK;
+}
+
+mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, mwj_mode mode,
+                           mwj_shares *shares, void *stream) {
+    (void)mode;
+    (void)stream;
+    if (!ctx || !shares) return MWJ_ERR_INVALID_ARG;
+    if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
+    if (kind == MWJ_LINEAR) return plan_linear_default(ctx, R, S, T, shares);
+    if (kind == MWJ_CYCLIC) return plan_cyclic_default(ctx, R, S, T, shares);
+    return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind");
+}
+
+}  // extern "C"
+
+namespace mwj {
+
+mwj_status check_out(mwj_ctx *ctx, const mwj_out *out, int arity) {
+    (void)arity;
+    if (!out->total) return fail(ctx, MWJ_ERR_INVALID_ARG, "out.total is NULL");
+    switch (out->mode) {
+        case MWJ_COUNT: return MWJ_OK;
+        case MWJ_COUNT_GROUP_BY_A:
+            if (!out->group_counts || out->a_domain <= 0)
+                return fail(ctx, MWJ_ERR_INVALID_ARG, "group_counts NULL or a_domain <= 0");
+            return MWJ_OK;
+        case MWJ_MATERIALIZE:
+            if (!out->n_rows || out->capacity < 0 || (out->capacity > 0 && !out->rows))
+                return fail(ctx, MWJ_ERR_INVALID_ARG, "rows/n_rows/capacity invalid");
+            if (((uintptr_t)out->rows & 15) != 0)
+                return fail(ctx, MWJ_ERR_INVALID_ARG, "rows must be 16-byte aligned");
+            return MWJ_OK;
+        default: return fail(ctx, MWJ_ERR_INVALID_ARG, "bad mode %d", (int)out->mode);
+    }
+}
+
+}  // namespace mwj

@@ -1,0 +1,37 @@
+// api_internal.h -- the context object and helpers shared by the C-ABI files.
+#pragma once
+
+#include <cstdarg>
+
+#include "internal.h"
+
+struct mwj_ctx {
+    mwj::DevInfo dev;
+    uint32_t seed;
+    mwj::Seeds seeds;
+    int32_t smem_bytes;
+    int32_t load_pct;
+    int64_t spin_limit;
+    mwj::DevStatus *status;   // device status word
+    char err[512];
+};
+
+namespace mwj {
+
+const char *status_text(int s);
+mwj_status fail(mwj_ctx *ctx, mwj_status s, const char *fmt, ...);
+mwj_status cuda_fail(mwj_ctx *ctx, cudaError_t e, const char *where);
+bool rel_ok(const mwj_rel &r);
+uint32_t pow2_at_least(uint64_t v);
+mwj_status check_out(mwj_ctx *ctx, const mwj_out *out, int arity);
+
+mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                               mwj_shares *sh);
+mwj_status plan_cyclic_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                               mwj_shares *sh);
+mwj_status cyc_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                         const mwj_shares *shares, mwj_mode mode, size_t *bytes);
+mwj_status cascade_workspace(mwj_ctx *ctx, int kind, const mwj_rel &R, const mwj_rel &S,
+                             const mwj_rel &T, mwj_mode mode, size_t *bytes);
+
+}  // namespace mwj

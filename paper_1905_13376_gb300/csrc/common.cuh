@@ -1,0 +1,201 @@
+// common.cuh -- shared device helpers of the multiway hash join library.
+//
+// Hashing (Section 4, "robust hash functions"; Fig. 2's two hash levels):
+// every attribute has its own seed; the top-level bucket of a key is
+// fastrange(mix32(key ^ seed), P) so that any bucket count P works, and the
+// slot of a key inside an on-chip table uses mix32 with a different seed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mwj.h"
+
+namespace mwj {
+
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;   // empty slot marker of u32-key tables
+constexpr uint64_t kEmpty64 = ~0ull;          // empty slot of packed (val<<32 | key) tables
+
+// Device status word: first error wins.
+struct DevStatus {
+    int32_t code;
+    int32_t pad;
+    int64_t aux;
+};
+
+__device__ __forceinline__ void set_status(DevStatus *st, int code, int64_t aux = 0) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->aux = aux;
+}
+
+// "lowbias32" integer finaliser (Wellons' hash-prospector family): a
+// bijection of uint32 with good avalanche.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Lemire's multiply-shift range reduction: uniform hash -> [0, n).
+__host__ __device__ __forceinline__ uint32_t fastrange(uint32_t h, uint32_t n) {
+    return (uint32_t)(((uint64_t)h * (uint64_t)n) >> 32);
+}
+
+__host__ __device__ __forceinline__ uint32_t bucket_of(int32_t key, uint32_t seed, uint32_t P) {
+    return fastrange(mix32((uint32_t)key ^ seed), P);
+}
+
+// Seeds of the per-attribute hash functions (top level) and of the slot hash
+// used inside tables.  Derived from the context seed.
+struct Seeds {
+    uint32_t A, B, C, D, slot, slot2;
+};
+
+inline Seeds make_seeds(uint32_t s) {
+    Seeds r;
+    r.A = mix32(s ^ 0x1b873593u);
+    r.B = mix32(s ^ 0x85ebca6bu);
+    r.C = mix32(s ^ 0xc2b2ae35u);
+    r.D = mix32(s ^ 0x27d4eb2fu);
+    r.slot = mix32(s ^ 0x165667b1u);
+    r.slot2 = mix32(s ^ 0x9e3779b9u);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Open-addressing table with u32 keys, power-of-two capacity `cap`
+// (mask = cap-1), linear probing.  The key value 0xFFFFFFFF (int32 -1) is the
+// empty marker, so that key is kept in the extra slot `cap`, whose keys[]
+// entry is used as its presence flag.  Arrays are sized cap + 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tbl_find(const uint32_t *keys, uint32_t mask, uint32_t k,
+                                        uint32_t seed) {
+    if (k == kEmptyKey) return keys[mask + 1] ? (int)(mask + 1) : -1;
+    uint32_t s = mix32(k ^ seed) & mask;
+    for (;;) {
+        uint32_t q = keys[s];
+        if (q == k) return (int)s;
+        if (q == kEmptyKey) return -1;
+        s = (s + 1) & mask;
+    }
+}
+
+// Insert-or-find; returns the slot and sets *fresh when this call claimed it.
+// The table must never be full (callers keep the fill below cap).
+__device__ __forceinline__ int tbl_insert(uint32_t *keys, uint32_t mask, uint32_t k,
+                                          uint32_t seed, bool *fresh) {
+    *fresh = false;
+    if (k == kEmptyKey) {
+        if (!keys[mask + 1]) {
+            if (atomicExch(&keys[mask + 1], 1u) == 0u) *fresh = true;
+        }
+        return (int)(mask + 1);
+    }
+    uint32_t s = mix32(k ^ seed) & mask;
+    for (;;) {
+        uint32_t q = keys[s];
+        if (q == k) return (int)s;
+        if (q == kEmptyKey) {
+            uint32_t old = atomicCAS(&keys[s], kEmptyKey, k);
+            if (old == kEmptyKey) { *fresh = true; return (int)s; }
+            if (old == k) return (int)s;
+        }
+        s = (s + 1) & mask;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed (count << 32 | key) slots, arbitrary capacity, used for the bucket
+// tables of T kept in global memory (images).  kEmpty64 never equals an
+// occupied slot because counts stay below 2^31.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t img_lookup(const uint64_t *img, uint32_t cap, uint32_t k,
+                                               uint32_t seed) {
+    if (cap == 0) return 0;
+    uint32_t s = fastrange(mix32(k ^ seed), cap);
+    for (;;) {
+        uint64_t v = __ldg((const unsigned long long *)(img + s));
+        if (v == kEmpty64) return 0;
+        if ((uint32_t)v == k) return (uint32_t)(v >> 32);
+        s = (s + 1 == cap) ? 0 : s + 1;
+    }
+}
+
+// Same lookup returning the slot index (for parallel arrays), -1 if absent.
+__device__ __forceinline__ int64_t img_slot(const uint64_t *img, uint32_t cap, uint32_t k,
+                                            uint32_t seed) {
+    if (cap == 0) return -1;
+    uint32_t s = fastrange(mix32(k ^ seed), cap);
+    for (;;) {
+        uint64_t v = __ldg((const unsigned long long *)(img + s));
+        if (v == kEmpty64) return -1;
+        if ((uint32_t)v == k) return (int64_t)s;
+        s = (s + 1 == cap) ? 0 : s + 1;
+    }
+}
+
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+    atomicAdd(p, v);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of a u64 (blockDim.x multiple of 32, <= 1024).  All threads
+// receive the result.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
+                                                            unsigned long long *scratch32) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch32[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    unsigned long long t = (threadIdx.x < (unsigned)nw) ? scratch32[threadIdx.x] : 0ull;
+    if (w == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) scratch32[0] = t;
+    __syncthreads();
+    t = scratch32[0];
+    __syncthreads();
+    return t;
+}
+
+// Block-wide exclusive scan of u32 values (one per thread); returns the
+// exclusive prefix, *total gets the block total.  scratch: >= 33 u32.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *scratch,
+                                                        uint32_t *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[w] = x;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    if (w == 0) {
+        uint32_t s = (lane < nw) ? scratch[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) scratch[lane] = s;   // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t warp_base = (w > 0) ? scratch[w - 1] : 0u;
+    uint32_t tot = scratch[nw - 1];
+    __syncthreads();
+    if (total) *total = tot;
+    return warp_base + x - v;
+}
+
+}  // namespace mwj

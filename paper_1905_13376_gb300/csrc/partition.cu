@@ -1,0 +1,328 @@
+// partition.cu -- radix hash partitioning of a relation (K1-K3).
+//
+// Algorithm 1's first three steps partition T by g(C), S by (H(B), g(C)) and
+// R by H(B); Section 5 partitions R by (H(A), G(B)), S by (G(B), F(C)) and
+// T by (F(C), H(A)) (Fig. 3).  All of these are one operation: bucket every
+// tuple by one or two hashed columns and write the relation out grouped by
+// bucket, with the bucket offsets.  The paper leaves the partitioner's
+// design open (Section 4); this is the GB300 one:
+//
+//   K1 hist     every CTA owns a contiguous chunk of tiles and counts its
+//               tuples per bucket in shared memory (one private histogram per
+//               warp when they fit, so warps do not contend)
+//   K2 scan     exclusive scan of the bucket-major (bucket, CTA) counts gives
+//               every CTA its write cursor in every bucket
+//   K3 scatter  every CTA re-reads its chunk tile by tile (128-bit loads),
+//               counting-sorts each 4096-tuple tile by bucket in shared memory
+//               and then writes each bucket's run with consecutive threads on
+//               consecutive addresses, so the scattered output is written in
+//               full sectors; for more than 4096 buckets the tile sort is
+//               skipped and tuples go straight to their cursor.
+//
+// The order of tuples inside a bucket is not specified (atomics decide it);
+// consumers never depend on it.
+#include "internal.h"
+
+namespace mwj {
+namespace {
+
+constexpr int PT = 512;               // threads per CTA
+constexpr int IPT = 8;                // tuples per thread per tile
+constexpr int TILE = PT * IPT;        // 4096 tuples
+constexpr uint32_t kStagedMaxP = 4096;
+constexpr int kWarps = PT / 32;
+
+__device__ __forceinline__ uint32_t bucket_tuple(int32_t x, int32_t y, const PartSpec &sp) {
+    int32_t k1 = sp.col1 ? y : x;
+    uint32_t b = bucket_of(k1, sp.seed1, sp.P1);
+    if (sp.col2 >= 0) {
+        int32_t k2 = sp.col2 ? y : x;
+        b = b * sp.P2 + bucket_of(k2, sp.seed2, sp.P2);
+    }
+    return b;
+}
+
+struct Chunk {
+    uint32_t begin, end;
+};
+
+__device__ __forceinline__ Chunk cta_chunk(uint32_t n, uint32_t tiles_per_cta) {
+    uint64_t b = (uint64_t)blockIdx.x * tiles_per_cta * TILE;
+    uint64_t e = b + (uint64_t)tiles_per_cta * TILE;
+    Chunk c;
+    c.begin = (uint32_t)(b < n ? b : n);
+    c.end = (uint32_t)(e < n ? e : n);
+    return c;
+}
+
+// K1: counts[b * G + cta] = number of this CTA's tuples in bucket b.
+template <bool WARP_PRIVATE>
+__global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
+                                                  const int32_t *__restrict__ y, uint32_t n,
+                                                  PartSpec sp, uint32_t tiles_per_cta,
+                                                  uint32_t *__restrict__ counts) {
+    extern __shared__ uint32_t hist[];
+    const uint32_t P = sp.P();
+    const uint32_t H = WARP_PRIVATE ? P * kWarps : P;
+    for (uint32_t i = threadIdx.x; i < H; i += PT) hist[i] = 0;
+    __syncthreads();
+    uint32_t *my = WARP_PRIVATE ? hist + (threadIdx.x >> 5) * P : hist;
+    Chunk c = cta_chunk(n, tiles_per_cta);
+    const bool vec = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    uint32_t i = c.begin + threadIdx.x * 4;
+    if (vec) {
+        for (; i + 3 < c.end; i += PT * 4) {
+            int4 xv = __ldg((const int4 *)(x + i));
+            int4 yv = __ldg((const int4 *)(y + i));
+            atomicAdd(&my[bucket_tuple(xv.x, yv.x, sp)], 1u);
+            atomicAdd(&my[bucket_tuple(xv.y, yv.y, sp)], 1u);
+            atomicAdd(&my[bucket_tuple(xv.z, yv.z, sp)], 1u);
+            atomicAdd(&my[bucket_tuple(xv.w, yv.w, sp)], 1u);
+        }
+    }
+    for (; i < c.end; i += PT * 4) {
+        for (uint32_t k = i; k < i + 4 && k < c.end; ++k)
+            atomicAdd(&my[bucket_tuple(__ldg(x + k), __ldg(y + k), sp)], 1u);
+    }
+    __syncthreads();
+    const uint32_t G = gridDim.x;
+    for (uint32_t b = threadIdx.x; b < P; b += PT) {
+        uint32_t s = 0;
+        if (WARP_PRIVATE) {
+#pragma unroll 4
+            for (int w = 0; w < kWarps; ++w) s += hist[w * P + b];
+        } else {
+            s = hist[b];
+        }
+        counts[(size_t)b * G + blockIdx.x] = s;
+    }
+}
+
+// bucket_off[b] = scanned[b * G], bucket_off[P] = n.
+__global__ void k_bucket_offsets(const uint32_t *__restrict__ scanned, uint32_t P, uint32_t G,
+                                 uint32_t n, uint32_t *__restrict__ bucket_off) {
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < P) bucket_off[b] = scanned[(size_t)b * G];
+    if (b == P) bucket_off[P] = n;
+}
+
+template <int PAY>
+struct PayT {
+    using T = uint32_t;
+};
+template <>
+struct PayT<PAY_PAIR> {
+    using T = uint2;
+};
+
+template <int PAY>
+__device__ __forceinline__ typename PayT<PAY>::T make_pay(int32_t x, int32_t y) {
+    if constexpr (PAY == PAY_PAIR) {
+        return make_uint2((uint32_t)x, (uint32_t)y);
+    } else if constexpr (PAY == PAY_X) {
+        return (uint32_t)x;
+    } else {
+        return (uint32_t)y;
+    }
+}
+
+// K3 (P <= 4096): tile-local counting sort in shared memory, coalesced runs.
+template <int PAY>
+__global__ void __launch_bounds__(PT) k_part_scatter_staged(
+    const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
+    uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
+    typename PayT<PAY>::T *__restrict__ out) {
+    using T = typename PayT<PAY>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t P = sp.P();
+    uint32_t *cur = (uint32_t *)smem;                    // P: global write cursor
+    uint32_t *cnt = cur + P;                             // P: tile counts
+    uint32_t *off = cnt + P;                             // P: tile offsets
+    T *stage = (T *)(smem + align256(3 * P * sizeof(uint32_t)));   // TILE
+    uint16_t *sbk = (uint16_t *)(stage + TILE);          // TILE bucket ids
+    __shared__ uint32_t scan_scratch[33];
+
+    const uint32_t G = gridDim.x;
+    for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] = scanned[(size_t)b * G + blockIdx.x];
+    Chunk c = cta_chunk(n, tiles_per_cta);
+    const bool vec = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    // entries of the per-thread scan over P
+    const uint32_t per = (P + PT - 1) / PT;
+
+    for (uint32_t t0 = c.begin; t0 < c.end; t0 += TILE) {
+        const uint32_t tn = min((uint32_t)TILE, c.end - t0);
+        for (uint32_t b = threadIdx.x; b < P; b += PT) cnt[b] = 0;
+        __syncthreads();
+        uint32_t bk[IPT], rk[IPT];
+        T pv[IPT];
+        // thread t handles tuples t0 + 4*t + {0..3} and t0 + 2048 + 4*t + {0..3}
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t li = (uint32_t)h * (TILE / 2) + threadIdx.x * 4;
+            uint32_t gi = t0 + li;
+            int32_t xs[4], ys[4];
+            if (vec && li + 3 < tn) {
+                int4 xv = __ldg((const int4 *)(x + gi));
+                int4 yv = __ldg((const int4 *)(y + gi));
+                xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
+                ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    xs[k] = (li + k < tn) ? __ldg(x + gi + k) : 0;
+                    ys[k] = (li + k < tn) ? __ldg(y + gi + k) : 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int j = h * 4 + k;
+                if (li + k < tn) {
+                    bk[j] = bucket_tuple(xs[k], ys[k], sp);
+                    rk[j] = atomicAdd(&cnt[bk[j]], 1u);
+                    pv[j] = make_pay<PAY>(xs[k], ys[k]);
+                } else {
+                    bk[j] = 0xFFFFFFFFu;
+                }
+            }
+        }
+        __syncthreads();
+        // exclusive scan of cnt[0..P) into off[]
+        {
+            uint32_t b0 = threadIdx.x * per;
+            uint32_t s = 0;
+            for (uint32_t k = 0; k < per; ++k)
+                if (b0 + k < P) s += cnt[b0 + k];
+            uint32_t base = block_excl_scan_u32(s, scan_scratch, nullptr);
+            for (uint32_t k = 0; k < per; ++k)
+                if (b0 + k < P) {
+                    off[b0 + k] = base;
+                    base += cnt[b0 + k];
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            if (bk[j] != 0xFFFFFFFFu) {
+                uint32_t p = off[bk[j]] + rk[j];
+                stage[p] = pv[j];
+                sbk[p] = (uint16_t)bk[j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < tn; e += PT) {
+            uint32_t b = sbk[e];
+            out[cur[b] + (e - off[b])] = stage[e];
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] += cnt[b];
+        __syncthreads();
+    }
+}
+
+// K3 (P > 4096): direct scatter through shared-memory cursors.
+template <int PAY>
+__global__ void __launch_bounds__(PT) k_part_scatter_direct(
+    const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
+    uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
+    typename PayT<PAY>::T *__restrict__ out) {
+    extern __shared__ uint32_t cur[];
+    const uint32_t P = sp.P();
+    const uint32_t G = gridDim.x;
+    for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] = scanned[(size_t)b * G + blockIdx.x];
+    __syncthreads();
+    Chunk c = cta_chunk(n, tiles_per_cta);
+    for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
+        int32_t xv = __ldg(x + i), yv = __ldg(y + i);
+        uint32_t b = bucket_tuple(xv, yv, sp);
+        uint32_t p = atomicAdd(&cur[b], 1u);
+        out[p] = make_pay<PAY>(xv, yv);
+    }
+}
+
+struct Geometry {
+    uint32_t G, tiles_per_cta;
+};
+
+Geometry geometry(int64_t n, int num_sms) {
+    uint64_t tiles = ((uint64_t)n + TILE - 1) / TILE;
+    if (tiles == 0) tiles = 1;
+    uint64_t gmax = (uint64_t)num_sms * 4;
+    uint64_t G = tiles < gmax ? tiles : gmax;
+    uint64_t tpc = (tiles + G - 1) / G;
+    G = (tiles + tpc - 1) / tpc;
+    return Geometry{(uint32_t)G, (uint32_t)tpc};
+}
+
+size_t hist_smem(uint32_t P, bool warp_private) {
+    return (size_t)P * sizeof(uint32_t) * (warp_private ? kWarps : 1);
+}
+
+template <int PAY>
+cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const PartSpec &sp,
+                           Geometry g, const uint32_t *scanned, void *out, cudaStream_t st) {
+    using T = typename PayT<PAY>::T;
+    const uint32_t P = sp.P();
+    if (P <= kStagedMaxP) {
+        size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint16_t);
+        auto kern = k_part_scatter_staged<PAY>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<g.G, PT, smem, st>>>(x, y, n, sp, g.tiles_per_cta, scanned, (T *)out);
+    } else {
+        size_t smem = P * sizeof(uint32_t);
+        auto kern = k_part_scatter_direct<PAY>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<g.G, PT, smem, st>>>(x, y, n, sp, g.tiles_per_cta, scanned, (T *)out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t part_scratch_bytes(int64_t n, uint32_t P, int num_sms) {
+    Geometry g = geometry(n, num_sms);
+    size_t cnt = (size_t)P * g.G;
+    return align256(cnt * sizeof(uint32_t)) + scan_scratch_bytes(cnt);
+}
+
+cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const PartSpec &sp,
+                     int payload, void *out, uint32_t *bucket_off, void *scratch,
+                     size_t scratch_bytes, int num_sms, cudaStream_t st) {
+    const uint32_t P = sp.P();
+    if (P == 0 || P > kMaxBuckets || n64 < 0 || n64 > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    if (scratch_bytes < part_scratch_bytes(n64, P, num_sms)) return cudaErrorInvalidValue;
+    const uint32_t n = (uint32_t)n64;
+    if (n == 0) {
+        return cudaMemsetAsync(bucket_off, 0, (P + 1) * sizeof(uint32_t), st);
+    }
+    Geometry g = geometry(n64, num_sms);
+    uint32_t *counts = (uint32_t *)scratch;
+    size_t ncnt = (size_t)P * g.G;
+    void *scan_tmp = (char *)scratch + align256(ncnt * sizeof(uint32_t));
+
+    const bool warp_private = hist_smem(P, true) <= 48 * 1024;
+    size_t hs = hist_smem(P, warp_private);
+    cudaError_t e;
+    if (warp_private) {
+        k_part_hist<true><<<g.G, PT, hs, st>>>(x, y, n, sp, g.tiles_per_cta, counts);
+    } else {
+        e = cudaFuncSetAttribute(k_part_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hs);
+        if (e != cudaSuccess) return e;
+        k_part_hist<false><<<g.G, PT, hs, st>>>(x, y, n, sp, g.tiles_per_cta, counts);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_excl_u32(counts, ncnt, scan_tmp, st)) != cudaSuccess) return e;
+    k_bucket_offsets<<<(P + 1 + 255) / 256, 256, 0, st>>>(counts, P, g.G, n, bucket_off);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (payload) {
+        case PAY_PAIR: return scatter_launch<PAY_PAIR>(x, y, n, sp, g, counts, out, st);
+        case PAY_X: return scatter_launch<PAY_X>(x, y, n, sp, g, counts, out, st);
+        default: return scatter_launch<PAY_Y>(x, y, n, sp, g, counts, out, st);
+    }
+}
+
+}  // namespace mwj

@@ -1,0 +1,138 @@
+"""Parity of the linear 3-way join (CUDA, through the C ABI) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_13376_gb300 import binding, datagen
+
+from gpu_util import cu, sorted_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.set_device(0)
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def check_all_modes(ctx, R, S, T, a_domain, shares=None, rows=True):
+    dR, dS, dT = cu(R), cu(S), cu(T)
+    want = oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=a_domain)
+    got = ctx.join3_linear(dR, dS, dT, "count", shares=shares)
+    assert int(got["total"].item()) == want["total"]
+    got = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=shares, a_domain=a_domain)
+    assert int(got["total"].item()) == want["total"]
+    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+    if rows:
+        n = want["total"]
+        wr = oracle.linear(R, S, T, oracle.MATERIALIZE, capacity=n)
+        got = ctx.join3_linear(dR, dS, dT, "rows", shares=shares, capacity=n + 5)
+        assert int(got["n_rows"].item()) == n
+        assert np.array_equal(sorted_rows(got["rows"].cpu().numpy()), wr["rows"])
+
+
+def test_uniform_small(ctx):
+    R, S, T = datagen.linear_uniform(n=5000, ad=300, bd=64, cd=64, dd=300, seed=11)
+    check_all_modes(ctx, R, S, T, 300)
+
+
+@pytest.mark.parametrize("shares", [(1, 1), (3, 1), (7, 5), (64, 1), (16, 16), (1, 200)])
+def test_share_invariance(ctx, shares):
+    R, S, T = datagen.linear_uniform(n=3000, ad=100, bd=50, cd=40, dd=100, seed=12)
+    check_all_modes(ctx, R, S, T, 100, shares=shares)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_tiny_with_duplicates(ctx, seed):
+    g = np.random.default_rng(seed)
+    nR, nS, nT = (int(g.integers(0, 40)) for _ in range(3))
+    dom = int(g.integers(1, 6))
+    R = (g.integers(0, 9, nR).astype(np.int32), g.integers(-2, dom, nR).astype(np.int32))
+    S = (g.integers(-2, dom, nS).astype(np.int32), g.integers(-2, dom, nS).astype(np.int32))
+    T = (g.integers(-2, dom, nT).astype(np.int32), g.integers(0, 9, nT).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 9)
+
+
+def test_extreme_keys(ctx):
+    vals = np.array([-2**31, 2**31 - 1, -1, 0, 1, -2], dtype=np.int32)
+    g = np.random.default_rng(7)
+    n = 900
+    R = (g.integers(0, 50, n).astype(np.int32), vals[g.integers(0, 6, n)])
+    S = (vals[g.integers(0, 6, n)], vals[g.integers(0, 6, n)])
+    T = (vals[g.integers(0, 6, n)], g.integers(-100, 100, n).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 50, rows=False)
+    check_all_modes(ctx, R[:1] + (R[1][:1],), S, T, 50)
+
+
+def test_empty_relations(ctx):
+    E = (np.zeros(0, np.int32), np.zeros(0, np.int32))
+    R, S, T = datagen.linear_uniform(n=100, ad=10, bd=5, cd=5, dd=10, seed=3)
+    for args in [(E, S, T), (R, E, T), (R, S, E), (E, E, E)]:
+        check_all_modes(ctx, *args, a_domain=10)
+
+
+def test_single_key_everywhere(ctx):
+    nR, nS, nT = 3000, 50, 2000
+    R = (np.arange(nR, dtype=np.int32) % 97, np.full(nR, 42, np.int32))
+    S = (np.full(nS, 42, np.int32), np.full(nS, -1, np.int32))
+    T = (np.full(nT, -1, np.int32), np.arange(nT, dtype=np.int32))
+    check_all_modes(ctx, R, S, T, 97, rows=False)
+    got = ctx.join3_linear(cu(R), cu(S), cu(T), "count")
+    assert int(got["total"].item()) == nR * nS * nT
+
+
+def test_many_distinct_keys_in_one_bucket_chunks(ctx):
+    # I = 1: all of R's ~60K distinct B values land in one on-chip table,
+    # which forces the chunked build; the result must not change
+    g = np.random.default_rng(5)
+    n = 60000
+    R = (g.integers(0, 1000, n).astype(np.int32), g.permutation(n).astype(np.int32))
+    S = (g.integers(0, n, n).astype(np.int32), g.integers(0, 3000, n).astype(np.int32))
+    T = (g.integers(0, 3000, n).astype(np.int32), g.integers(0, 10, n).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 1000, shares=(1, 1))
+    check_all_modes(ctx, R, S, T, 1000, shares=(2, 3))
+
+
+def test_skewed_zipf(ctx):
+    g = np.random.default_rng(8)
+    q = datagen.random_query(g, "linear", size_lo=20000, size_hi=40000, dom_lo=200, dom_hi=2000,
+                             zipf=True, zipf_s=1.4)
+    check_all_modes(ctx, q.R, q.S, q.T, q.domains[0], rows=False)
+
+
+def test_domain_error(ctx):
+    R = (np.array([0, 5, 1], np.int32), np.array([1, 1, 2], np.int32))
+    S = (np.array([1, 2], np.int32), np.array([2, 2], np.int32))
+    T = (np.array([2], np.int32), np.array([0], np.int32))
+    with pytest.raises(binding.MwjError) as ei:
+        ctx.join3_linear(cu(R), cu(S), cu(T), "group_by_a", a_domain=5)
+    assert ei.value.status == binding.MWJ_ERR_DOMAIN
+
+
+def test_capacity_error_reports_exact_count(ctx):
+    R, S, T = datagen.linear_uniform(n=500, ad=10, bd=8, cd=8, dd=10, seed=4)
+    n = oracle.linear(R, S, T)["total"]
+    with pytest.raises(binding.MwjError) as ei:
+        ctx.join3_linear(cu(R), cu(S), cu(T), "rows", capacity=n - 1)
+    assert ei.value.status == binding.MWJ_ERR_CAPACITY
+    assert str(n) in str(ei.value)
+
+
+def test_aliased_self_join(ctx):
+    # F join F join F with R = S = T the same device arrays
+    g = np.random.default_rng(2)
+    F = (g.integers(0, 700, 20000).astype(np.int32), g.integers(0, 700, 20000).astype(np.int32))
+    dF = cu(F)
+    want = oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=700)
+    got = ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=700)
+    assert int(got["total"].item()) == want["total"]
+    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+
+
+def test_uniform_config_full_size(ctx):
+    R, S, T = datagen.linear_uniform()
+    check_all_modes(ctx, R, S, T, 1 << 20, rows=False)
