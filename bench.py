@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 3-way hash join: input tuples/s of the linear
+friends-of-friends-of-friends self-join F |x| F |x| F (COUNT(*) GROUP BY A)
+on a synthetic power-law graph of 2^20 vertices (Zipf s=1.1 degrees capped at
+4096, mean degree 32, ~3.3e7 directed edges), multiway vs cascade, exact
+counts.
+
+Prints one JSON line.  `python bench.py --gpus N --steps K --warmup W`; under
+torchrun every rank runs its own replica of the workload (the join is one
+problem per GPU; replicas only) and rank 0 reports the aggregate.
+
+--impl reference times the CPU oracle (single-threaded C hash join) on the
+same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3-way join input tuples/s + % HBM roofline, multiway vs cascade, exact counts"
+UNIT = "tuples/s"
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels from one ncu capture, valid only for the library sources they were
+# taken from (digest of csrc/ + include/).  Filled from profiles/.
+TRAFFIC = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def lib_digest():
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1905_13376_gb300", "csrc", "*")) +
+                    [os.path.join(ROOT, "include", "mwj.h")]):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def make_workload(args):
+    from paper_1905_13376_gb300 import datagen
+    F = datagen.chung_lu_directed(n_vertices=args.vertices, mean_degree=32.0)
+    desc = (f"linear self-join F|x|F|x|F, COUNT(*) GROUP BY A; F = directed power-law graph, "
+            f"{args.vertices} vertices, Zipf s=1.1 degrees capped at 4096, mean degree 32, "
+            f"{len(F[0])} edges (int32 src,dst)")
+    return F, desc
+
+
+def algorithmic_bytes(name, nR, nS, nT, a_domain, tslots, launches):
+    """Bytes a kernel must move per step (each buffer once at its stored size)."""
+    if name == "lin_probe_groupby":
+        return 8 * nR + 8 * nS + 8 * tslots + 8 * a_domain
+    if name == "lin_probe_count":
+        return 8 * nR + 8 * nS + 8 * tslots
+    if name == "part_scatter":
+        # R and S: read 8 B + write 8 B per tuple; T (keys only): read 4 + write 4
+        return 16 * nR + 16 * nS + 8 * nT
+    if name == "part_hist":
+        return 4 * (nR + nS + nT)
+    if name == "t_aggregate":
+        return 4 * nT + 8 * nT
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1905_13376_gb300 import binding
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    F, desc = make_workload(args)
+    n = len(F[0])
+    a_domain = args.vertices
+    dF = tuple(torch.from_numpy(c).to(dev) for c in F)
+    ctx = binding.Context(local_rank)
+    shares = tuple(args.shares) if args.shares else ctx.plan_shares(binding.MWJ_LINEAR, dF, dF, dF,
+                                                                    binding.MWJ_COUNT_GROUP_BY_A)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(sync=False):
+        return ctx.join3_linear(dF, dF, dF, "group_by_a", shares=shares, a_domain=a_domain,
+                                sync=sync)
+
+    # exactness check once (device result vs the oracle is in the tests; here
+    # the group counts must at least sum to the total)
+    r = step(sync=True)
+    total = int(r["total"].item())
+    assert int(r["counts"].sum().item()) == total
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.reset_phase_times()
+    launches0 = ctx.launch_count()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.launch_count() - launches0
+    phases = ctx.phase_times()
+    ctx.set_profiling(False)
+
+    # end to end through the C ABI from pinned host memory: H2D of F, the
+    # join, D2H of the group counts and the total, every step
+    hF = tuple(torch.from_numpy(c).pin_memory() for c in F)
+    hcnt = torch.empty(a_domain, dtype=torch.int64).pin_memory()
+    htot = torch.empty(1, dtype=torch.int64).pin_memory()
+    eF = tuple(torch.empty_like(c) for c in dF)
+
+    def e2e_step():
+        for h, d in zip(hF, eF):
+            d.copy_(h, non_blocking=True)
+        rr = ctx.join3_linear(eF, eF, eF, "group_by_a", shares=shares, a_domain=a_domain,
+                              sync=False)
+        hcnt.copy_(rr["counts"], non_blocking=True)
+        htot.copy_(rr["total"], non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / args.steps
+    assert int(htot.item()) == total
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+
+    tuples = 3 * n
+    value = tuples * world / (ms * 1e-3)
+    peak, peak_kind = peaks()
+    # T's single table: 2^k >= 2 x (distinct C values) slots of 8 bytes
+    dc = int(np.count_nonzero(np.bincount(F[0], minlength=a_domain)))
+    tslots = 16
+    while tslots < 2 * dc:
+        tslots *= 2
+    # dominant kernel and its roofline
+    per_step = {k: v[0] / args.steps for k, v in phases.items()}
+    dom = max(per_step, key=per_step.get) if per_step else None
+    roof = None
+    if dom:
+        ab = algorithmic_bytes(dom, n, n, n, a_domain, tslots, phases[dom][1] / args.steps)
+        if ab is not None:
+            achieved = ab / (per_step[dom] * 1e-3) / 1e9
+            tr = TRAFFIC.get(dom)
+            traffic = tr["bytes_per_step"] if tr and tr.get("digest") == lib_digest() else None
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": traffic, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_step": ab,
+                    "ms_per_step": round(per_step[dom], 4)}
+    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4),
+                   "launches_per_step": v[1] / args.steps} for k, v in phases.items()}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded power-law graph)",
+        "config": {"workload": desc, "impl": "multiway (single-step 3-way hash join)",
+                   "shares": list(shares), "tuples_per_step": tuples, "result_total": total,
+                   "result_tuples_per_s": total * world / (ms * 1e-3),
+                   "l2": "inputs (268 MB) and partitions exceed the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "kernels": kernels,
+        "e2e": {"value": tuples * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    return out, F
+
+
+def cpu_baseline(F, a_domain, budget_s=30.0):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=a_domain)
+    dt = time.perf_counter() - t0
+    n = len(F[0])
+    return {"value": 3 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the full workload once ({3 * n} input tuples, {dt:.2f} s, 1 thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    F, desc = make_workload(args)
+    import oracle
+    n = len(F[0])
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=args.vertices)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = 3 * n / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded power-law graph)",
+            "config": {"workload": desc, "impl": "CPU oracle, single-threaded C hash join"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the full workload per step ({3 * n} input tuples)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--vertices", type=int, default=1 << 20)
+    ap.add_argument("--shares", type=int, nargs=2, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    out, F = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(F, args.vertices)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,23 @@ mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel
  * the context; valid until the next call). */
 const char *mwj_last_error(mwj_ctx *ctx);
 
+/* Launch accounting and per-kernel timing, for benchmarks and profiles.  No
+ * counterpart in the paper (its numbers come from a performance model).
+ * mwj_set_profiling(ctx, 1) makes every kernel the context launches record a
+ * CUDA event pair on its stream (a pool of 2^15 launches; later launches are
+ * counted but not timed until mwj_reset_phase_times).  mwj_launch_count
+ * returns the number of kernels the context has launched since it was
+ * created, whether or not profiling is on.  mwj_get_phase_times synchronises
+ * on the recorded events and fills up to `max` entries of per-kernel-name
+ * totals (milliseconds and launches; names stay valid until the next call on
+ * the context); it returns the number of distinct kernel names, or -1 for a
+ * NULL context. */
+mwj_status mwj_set_profiling(mwj_ctx *ctx, int enable);
+long long mwj_launch_count(mwj_ctx *ctx);
+int mwj_get_phase_times(mwj_ctx *ctx, const char **names, double *ms, long long *launches,
+                        int max);
+mwj_status mwj_reset_phase_times(mwj_ctx *ctx);
+
 /* Library version string, e.g. "mwj 0.1 sm_103a". */
 const char *mwj_version(void);
 

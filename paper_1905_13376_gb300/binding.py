@@ -83,6 +83,12 @@ _SIGS = {
     "mwj_plan_shares": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel, ctypes.c_int,
                                        ctypes.POINTER(mwj_shares), _P]),
     "mwj_last_error": (ctypes.c_char_p, [_P]),
+    "mwj_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "mwj_launch_count": (ctypes.c_longlong, [_P]),
+    "mwj_get_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+    "mwj_reset_phase_times": (ctypes.c_int, [_P]),
     "mwj_version": (ctypes.c_char_p, []),
 }
 
@@ -169,6 +175,24 @@ class Context:
     def _check(self, st):
         if st != MWJ_OK:
             raise MwjError(st, self.lib.mwj_last_error(self.h).decode())
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.mwj_set_profiling(self.h, 1 if on else 0))
+
+    def launch_count(self) -> int:
+        return int(self.lib.mwj_launch_count(self.h))
+
+    def phase_times(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last reset."""
+        n = self.lib.mwj_get_phase_times(self.h, None, None, None, 0)
+        names = (ctypes.c_char_p * max(n, 1))()
+        ms = (ctypes.c_double * max(n, 1))()
+        cnt = (ctypes.c_longlong * max(n, 1))()
+        n = self.lib.mwj_get_phase_times(self.h, names, ms, cnt, n)
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(n)}
+
+    def reset_phase_times(self):
+        self._check(self.lib.mwj_reset_phase_times(self.h))
 
     def workspace(self, nbytes: int):
         import torch

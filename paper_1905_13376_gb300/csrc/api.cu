@@ -63,13 +63,15 @@ namespace {
 struct LinPlan {
     uint32_t I, J, JT;
     bool rows;
+    bool single;   // T in one L2-resident table (S not split by C, count modes)
 };
 
 // bucket count of T's tables: small buckets so that each is aggregated in
 // one CTA's shared memory; equal to J when S is split by g(C) as well.
-uint32_t t_buckets(int64_t nT, uint32_t J) {
+uint32_t t_buckets(int64_t nT, uint32_t J, bool single) {
     if (J > 1) return J;
-    uint64_t want = (uint64_t)(nT + 2047) / 2048;
+    const uint64_t per = single ? 8192 : 2048;
+    uint64_t want = (uint64_t)(nT + per - 1) / per;
     uint32_t p = pow2_at_least(want ? want : 1);
     return p > kMaxBuckets ? kMaxBuckets : p;
 }
@@ -79,6 +81,7 @@ struct LinLayout {
     uint2 *Sp; uint32_t *offS;
     uint32_t *Tk; uint2 *Tp; uint32_t *offT;
     uint64_t *img; uint32_t *capT; uint32_t *startT; int32_t *dlist;
+    uint32_t *ekey, *ecnt, *ecount, *meta;
     void *pscratch; size_t pscratch_bytes;
     unsigned long long *rowcount, *base; void *sscratch;
 };
@@ -97,8 +100,18 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
         L.Tp = nullptr;
     }
     L.offT = A.take<uint32_t>(p.JT + 1);
-    L.img = A.take<uint64_t>(2 * (size_t)T.n + 4);
-    L.capT = A.take<uint32_t>(p.JT + 1);
+    if (p.single) {
+        L.img = A.take<uint64_t>(single_table_slots(T.n));
+        L.capT = nullptr;
+        L.ekey = A.take<uint32_t>(T.n + 4);
+        L.ecnt = A.take<uint32_t>(T.n + 4);
+        L.ecount = A.take<uint32_t>(p.JT + 1);
+        L.meta = A.take<uint32_t>(4);
+    } else {
+        L.img = A.take<uint64_t>(2 * (size_t)T.n + 4);
+        L.capT = A.take<uint32_t>(p.JT + 1);
+        L.ekey = L.ecnt = L.ecount = L.meta = nullptr;
+    }
     if (p.rows) {
         L.startT = A.take<uint32_t>(2 * (size_t)T.n + 4);
         L.dlist = A.take<int32_t>(T.n + 4);
@@ -129,10 +142,10 @@ mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S,
                                mwj_shares *sh) {
     (void)S;
     (void)T;
-    // R bucket tables of 2^13 slots hold up to ~4K distinct B values; aim for
-    // ~2K tuples of R per bucket and at least two CTAs per SM.
-    uint64_t want = (uint64_t)(R.n + 2047) / 2048;
-    uint64_t minb = (uint64_t)ctx->dev.num_sms * 2;
+    // R bucket tables of 2^12 slots hold up to ~2K distinct B values; aim for
+    // ~16K tuples of R per bucket and at least four buckets per SM.
+    uint64_t want = (uint64_t)(R.n + 16383) / 16384;
+    uint64_t minb = (uint64_t)ctx->dev.num_sms * 4;
     if (want < minb) want = minb;
     uint32_t I = pow2_at_least(want);
     if (I > 16384) I = 16384;
@@ -186,6 +199,13 @@ mwj_status mwj_create(mwj_ctx **out, const mwj_config *cfg) {
     ctx->smem_bytes = c.smem_bytes;
     ctx->load_pct = c.load_pct > 0 ? c.load_pct : 50;
     ctx->spin_limit = c.spin_limit > 0 ? c.spin_limit : (1ll << 26);
+    // on-chip R table: 2^cap_log2 slots of 12 bytes (GROUP BY A), default 4096
+    ctx->cap_log2 = 12;
+    if (c.smem_bytes > 0) {
+        uint32_t l = 9;
+        while (l < 14 && (12ull << (l + 1)) <= (unsigned long long)c.smem_bytes) ++l;
+        ctx->cap_log2 = l;
+    }
     e = cudaMalloc(&ctx->status, sizeof(DevStatus));
     if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
     e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
@@ -202,6 +222,37 @@ mwj_status mwj_destroy(mwj_ctx *ctx) {
 }
 
 const char *mwj_last_error(mwj_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+mwj_status mwj_set_profiling(mwj_ctx *ctx, int enable) {
+    if (!ctx) return MWJ_ERR_INVALID_ARG;
+    ctx->prof.enable(enable != 0, 1 << 15);
+    return MWJ_OK;
+}
+
+long long mwj_launch_count(mwj_ctx *ctx) { return ctx ? ctx->prof.launches : -1; }
+
+int mwj_get_phase_times(mwj_ctx *ctx, const char **names, double *ms, long long *launches,
+                        int max) {
+    if (!ctx) return -1;
+    ctx->prof.resolve();
+    int i = 0;
+    for (auto &kv : ctx->prof.acc) {
+        if (i < max) {
+            if (names) names[i] = kv.first.c_str();
+            if (ms) ms[i] = kv.second.first;
+            if (launches) launches[i] = kv.second.second;
+        }
+        ++i;
+    }
+    return i;
+}
+
+mwj_status mwj_reset_phase_times(mwj_ctx *ctx) {
+    if (!ctx) return MWJ_ERR_INVALID_ARG;
+    ctx->prof.resolve();
+    ctx->prof.acc.clear();
+    return MWJ_OK;
+}
 
 mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream) {
     if (!ctx) return MWJ_ERR_INVALID_ARG;
@@ -231,8 +282,9 @@ mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_
         LinPlan p;
         mwj_status s = lin_check_shares(ctx, &sh, &p.I, &p.J);
         if (s != MWJ_OK) return s;
-        p.JT = t_buckets(T.n, p.J);
         p.rows = (mode == MWJ_MATERIALIZE);
+        p.single = (p.J == 1 && !p.rows);
+        p.JT = t_buckets(T.n, p.J, p.single);
         Arena A(nullptr, 0);
         LinLayout L;
         *bytes = lin_layout(A, p, R, S, T, ctx->dev.num_sms, L);
@@ -248,6 +300,7 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
                             const mwj_shares *shares, const mwj_out *out, void *workspace,
                             size_t ws_bytes, void *stream) {
     if (!ctx || !out) return MWJ_ERR_INVALID_ARG;
+    ApiScope api_scope(&ctx->prof);
     if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
     mwj_status s = check_out(ctx, out, 4);
     if (s != MWJ_OK) return s;
@@ -257,8 +310,9 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     LinPlan p;
     s = lin_check_shares(ctx, &sh, &p.I, &p.J);
     if (s != MWJ_OK) return s;
-    p.JT = t_buckets(T.n, p.J);
     p.rows = (out->mode == MWJ_MATERIALIZE);
+    p.single = (p.J == 1 && !p.rows);
+    p.JT = t_buckets(T.n, p.J, p.single);
     Arena A(workspace, ws_bytes);
     LinLayout L;
     lin_layout(A, p, R, S, T, ctx->dev.num_sms, L);
@@ -286,15 +340,22 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
-    // T's bucket tables
-    e = tables_build(L.Tk, L.Tp, L.offT, p.JT, sd.slot2, L.img, L.capT, L.startT, L.dlist,
-                     ctx->dev.num_sms, st);
+    // T's tables
+    if (p.single)
+        e = single_table_build(L.Tk, L.offT, p.JT, sd.slot2, L.ekey, L.ecnt, L.ecount, L.meta, L.img,
+                               ctx->status, ctx->dev.num_sms, st);
+    else
+        e = tables_build(L.Tk, L.Tp, L.offT, p.JT, sd.slot2, L.img, L.capT, L.startT, L.dlist,
+                         ctx->status, ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "T tables");
 
     LinArgs g{};
     g.Rp = L.Rp; g.offR = L.offR; g.Sp = L.Sp; g.offS = L.offS; g.I = p.I; g.JS = p.J;
-    g.t = TImg{L.img, L.offT, L.capT, L.startT, L.dlist, p.JT, sd.C, sd.slot2};
-    g.cap_log2 = 13;
+    if (p.single)
+        g.t = TImg{L.img, nullptr, nullptr, nullptr, nullptr, L.meta, 0u, sd.C, sd.slot2};
+    else
+        g.t = TImg{L.img, L.offT, L.capT, L.startT, L.dlist, nullptr, p.JT, sd.C, sd.slot2};
+    g.cap_log2 = ctx->cap_log2;
     g.seed_slot = sd.slot;
     g.a_domain = out->a_domain;
     g.cnt = (unsigned long long *)out->group_counts;

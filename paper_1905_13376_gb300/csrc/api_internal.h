@@ -4,6 +4,7 @@
 #include <cstdarg>
 
 #include "internal.h"
+#include "prof.h"
 
 struct mwj_ctx {
     mwj::DevInfo dev;
@@ -12,7 +13,9 @@ struct mwj_ctx {
     int32_t smem_bytes;
     int32_t load_pct;
     int64_t spin_limit;
+    uint32_t cap_log2;        // on-chip R table size (log2 slots)
     mwj::DevStatus *status;   // device status word
+    mwj::Profiler prof;
     char err[512];
 };
 

@@ -74,16 +74,18 @@ __device__ __forceinline__ int tbl_find(const uint32_t *keys, uint32_t mask, uin
                                         uint32_t seed) {
     if (k == kEmptyKey) return keys[mask + 1] ? (int)(mask + 1) : -1;
     uint32_t s = mix32(k ^ seed) & mask;
-    for (;;) {
+    for (uint32_t it = 0; it <= mask; ++it) {   // bounded: a full table ends the search
         uint32_t q = keys[s];
         if (q == k) return (int)s;
         if (q == kEmptyKey) return -1;
         s = (s + 1) & mask;
     }
+    return -1;
 }
 
 // Insert-or-find; returns the slot and sets *fresh when this call claimed it.
-// The table must never be full (callers keep the fill below cap).
+// Callers keep the fill below cap; should the table be full anyway the
+// search stops after cap probes and returns -1.
 __device__ __forceinline__ int tbl_insert(uint32_t *keys, uint32_t mask, uint32_t k,
                                           uint32_t seed, bool *fresh) {
     *fresh = false;
@@ -94,7 +96,7 @@ __device__ __forceinline__ int tbl_insert(uint32_t *keys, uint32_t mask, uint32_
         return (int)(mask + 1);
     }
     uint32_t s = mix32(k ^ seed) & mask;
-    for (;;) {
+    for (uint32_t it = 0; it <= mask; ++it) {
         uint32_t q = keys[s];
         if (q == k) return (int)s;
         if (q == kEmptyKey) {
@@ -104,6 +106,14 @@ __device__ __forceinline__ int tbl_insert(uint32_t *keys, uint32_t mask, uint32_
         }
         s = (s + 1) & mask;
     }
+    return -1;
+}
+
+// Tuples per build round for a table of cap slots: at most cap/4, so that a
+// round started below 3/4 fill can never fill the table.
+__host__ __device__ __forceinline__ uint32_t round_tuples(uint32_t cap, uint32_t max_round) {
+    uint32_t r = cap / 4;
+    return r < max_round ? r : max_round;
 }
 
 // ---------------------------------------------------------------------------
@@ -115,12 +125,13 @@ __device__ __forceinline__ uint32_t img_lookup(const uint64_t *img, uint32_t cap
                                                uint32_t seed) {
     if (cap == 0) return 0;
     uint32_t s = fastrange(mix32(k ^ seed), cap);
-    for (;;) {
+    for (uint32_t it = 0; it < cap; ++it) {
         uint64_t v = __ldg((const unsigned long long *)(img + s));
         if (v == kEmpty64) return 0;
         if ((uint32_t)v == k) return (uint32_t)(v >> 32);
         s = (s + 1 == cap) ? 0 : s + 1;
     }
+    return 0;
 }
 
 // Same lookup returning the slot index (for parallel arrays), -1 if absent.
@@ -128,12 +139,13 @@ __device__ __forceinline__ int64_t img_slot(const uint64_t *img, uint32_t cap, u
                                             uint32_t seed) {
     if (cap == 0) return -1;
     uint32_t s = fastrange(mix32(k ^ seed), cap);
-    for (;;) {
+    for (uint32_t it = 0; it < cap; ++it) {
         uint64_t v = __ldg((const unsigned long long *)(img + s));
         if (v == kEmpty64) return -1;
         if ((uint32_t)v == k) return (int64_t)s;
         s = (s + 1 == cap) ? 0 : s + 1;
     }
+    return -1;
 }
 
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {

@@ -76,3 +76,24 @@ struct Arena {
 };
 
 }  // namespace mwj
+
+// ---- launch accounting and optional per-kernel timing ----------------------
+// Every kernel launch of the library sits inside a ProfScope.  The scope
+// always counts the launch; when profiling is enabled on the calling
+// context it also records a CUDA event pair on the launch stream, resolved
+// later by mwj_get_phase_times().
+namespace mwj {
+
+struct Profiler;
+Profiler *current_profiler();
+void set_current_profiler(Profiler *p);
+
+struct ProfScope {
+    Profiler *p;
+    int slot;
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    cudaStream_t st;
+};
+
+}  // namespace mwj

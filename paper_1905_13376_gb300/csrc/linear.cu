@@ -27,80 +27,130 @@ namespace {
 constexpr int LT = 512;          // threads per CTA
 constexpr int ROUND = LT * 4;    // R tuples inserted per build round
 
-// Calls f(tuple) for every tuple of p[s0, s1), two tuples per 128-bit load.
-template <typename F>
-__device__ __forceinline__ void stream_pairs(const uint2 *__restrict__ p, uint32_t s0, uint32_t s1,
-                                             F &&f) {
-    if (s0 >= s1) return;
-    uint32_t a = s0;
-    if (a & 1u) {
-        if (threadIdx.x == 0) f(p[a]);
-        ++a;
-    }
-    const uint32_t npair = (s1 - a) >> 1;
-    const uint4 *p4 = (const uint4 *)(p + a);
-    uint32_t q = threadIdx.x;
-    for (; q + LT < npair; q += 2 * LT) {
-        uint4 u = __ldg(p4 + q);
-        uint4 v = __ldg(p4 + q + LT);
-        f(make_uint2(u.x, u.y));
-        f(make_uint2(u.z, u.w));
-        f(make_uint2(v.x, v.y));
-        f(make_uint2(v.z, v.w));
-    }
-    for (; q < npair; q += LT) {
-        uint4 u = __ldg(p4 + q);
-        f(make_uint2(u.x, u.y));
-        f(make_uint2(u.z, u.w));
-    }
-    if ((s1 - a) & 1u) {
-        if (threadIdx.x == LT - 1) f(p[s1 - 1]);
-    }
-}
-
-struct SmemTbl {
-    uint32_t *keys;   // cap + 1
-    uint32_t mask;
-};
-
 // Clear the table; values are cleared by the caller.
 __device__ __forceinline__ void tbl_clear(uint32_t *keys, uint32_t cap) {
     for (uint32_t s = threadIdx.x; s < cap; s += LT) keys[s] = kEmptyKey;
     if (threadIdx.x == 0) keys[cap] = 0u;
 }
 
-// Insert R tuples [pos, ...) in rounds until the table holds more than half
-// of cap distinct keys or the chunk reaches max_tuples; returns the chunk end.
+// Insert R tuples [pos, ...) in rounds of round_tuples(cap) tuples while the
+// table stays at most 3/4 full (so it is never full) and the chunk stays
+// within max_tuples; returns the chunk end, which is always past pos.
 // on_insert(slot, tuple) runs for every inserted tuple.  Ends with a barrier.
 template <typename F>
 __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, uint32_t pos,
                                                 uint32_t r1, uint32_t *keys, uint32_t cap,
                                                 uint32_t seed, uint32_t max_tuples,
-                                                uint32_t *nd, F &&on_insert) {
+                                                uint32_t *nd, DevStatus *st, F &&on_insert) {
     const uint32_t mask = cap - 1;
+    const uint32_t rt = round_tuples(cap, ROUND);
     uint32_t cend = pos;
     for (;;) {
         __syncthreads();
         const uint32_t filled = *nd;
         __syncthreads();   // every thread has read the count before this round adds to it
-        if (cend >= r1 || filled > cap / 2 || cend - pos + ROUND > max_tuples) break;
+        if (cend >= r1 || filled + rt > cap - cap / 4 || cend - pos + rt > max_tuples) break;
         uint32_t fresh_n = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            uint32_t idx = cend + threadIdx.x + k * LT;
-            if (idx < r1) {
+            uint32_t li = threadIdx.x + k * LT;
+            uint32_t idx = cend + li;
+            if (li < rt && idx < r1) {
                 uint2 t = __ldg(Rp + idx);
                 bool fresh;
                 int slot = tbl_insert(keys, mask, t.y, seed, &fresh);
+                if (slot < 0) {
+                    set_status(st, MWJ_ERR_CHECK, 1);
+                    continue;
+                }
                 fresh_n += fresh;
                 on_insert(slot, t);
             }
         }
         fresh_n = warp_sum(fresh_n);
         if ((threadIdx.x & 31) == 0 && fresh_n) atomicAdd(nd, fresh_n);
-        cend += ROUND;
+        cend += rt;
     }
     return cend < r1 ? cend : r1;
+}
+
+// Tuples p[s0, s1) in batches of up to 8 consecutive tuples per thread
+// (thread t takes [b + 8t, b + 8t + 8) of every 8*LT-tuple round), loaded with
+// 128-bit loads; f(t, n) gets the batch and its length.
+template <typename F>
+__device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint32_t s0, uint32_t s1,
+                                               F &&f) {
+    if (s0 >= s1) return;
+    uint32_t a = s0;
+    uint2 t[8];
+    if (a & 1u) {
+        if (threadIdx.x == 0) {
+            t[0] = __ldg(p + a);
+            f(t, 1);
+        }
+        ++a;
+    }
+    for (uint32_t b = a + 8 * threadIdx.x; b < s1; b += 8 * LT) {
+        const uint32_t n = min(8u, s1 - b);
+        if (n == 8) {
+            const uint4 *q = (const uint4 *)(p + b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint4 u = __ldg(q + k);
+                t[2 * k] = make_uint2(u.x, u.y);
+                t[2 * k + 1] = make_uint2(u.z, u.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < (int)n) t[k] = __ldg(p + b + k);
+        }
+        f(t, n);
+    }
+}
+
+// deg_T of the 8 C values of a batch: the first probe of every tuple is
+// issued before any is consumed (one L2 round trip for the whole batch in
+// the common case).
+__device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const uint2 (&t)[8],
+                                          const int (&sl)[8], uint32_t n, uint32_t (&dT)[8]) {
+    if (T.J == 0) {
+        uint32_t ts[8];
+        unsigned long long v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k < (int)n && sl[k] >= 0) {
+                ts[k] = mix32(t[k].y ^ T.seed_slot) & tmask;
+                v[k] = __ldg((const unsigned long long *)(T.img + ts[k]));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            dT[k] = 0;
+            if (k < (int)n && sl[k] >= 0) {
+                unsigned long long x = v[k];
+                uint32_t s = ts[k];
+                for (uint32_t it = 0; it < tmask && x != kEmpty64 && (uint32_t)x != t[k].y; ++it) {
+                    s = (s + 1) & tmask;
+                    x = __ldg((const unsigned long long *)(T.img + s));
+                }
+                if ((uint32_t)x != t[k].y) x = kEmpty64;
+                dT[k] = (x == kEmpty64) ? 0u : (uint32_t)(x >> 32);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            dT[k] = (k < (int)n && sl[k] >= 0) ? timg_deg(T, (int32_t)t[k].y) : 0u;
+    }
+}
+
+// 64-bit add into (hi, lo) 32-bit shared counters, exact modulo 2^64.
+__device__ __forceinline__ void add_u64_split(uint32_t *lo, uint32_t *hi, unsigned long long v) {
+    uint32_t l = (uint32_t)v, h = (uint32_t)(v >> 32);
+    uint32_t old = atomicAdd(lo, l);
+    if (old + l < old) ++h;
+    if (h) atomicAdd(hi, h);
 }
 
 // COUNT (MODE 0) and GROUP BY A (MODE 1).  One CTA per R bucket.
@@ -108,16 +158,18 @@ template <int MODE>
 __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t cap = 1u << g.cap_log2;
+    const size_t arr = align256((cap + 1) * sizeof(uint32_t));
     uint32_t *keys = (uint32_t *)smem;
-    unsigned char *vbase = smem + align256((cap + 1) * sizeof(uint32_t));
-    uint32_t *deg = (uint32_t *)vbase;                            // MODE 0
-    unsigned long long *w = (unsigned long long *)vbase;          // MODE 1
+    uint32_t *deg = (uint32_t *)(smem + arr);          // MODE 0
+    uint32_t *wlo = (uint32_t *)(smem + arr);          // MODE 1
+    uint32_t *whi = (uint32_t *)(smem + 2 * arr);      // MODE 1
     __shared__ uint32_t nd;
     __shared__ unsigned long long red[32];
 
     const uint32_t i = blockIdx.x;
     const uint32_t r0 = g.offR[i], r1 = g.offR[i + 1];
     const uint32_t s0 = g.offS[(size_t)i * g.JS], s1 = g.offS[(size_t)(i + 1) * g.JS];
+    const uint32_t tmask = (g.t.J == 0) ? __ldg(g.t.meta) : 0u;
     unsigned long long acc = 0;
     const uint32_t mask = cap - 1;
 
@@ -125,10 +177,15 @@ __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
         for (uint32_t pos = r0; pos < r1;) {
             tbl_clear(keys, cap);
             for (uint32_t s = threadIdx.x; s <= cap; s += LT) {
-                if (MODE == 0) deg[s] = 0u; else w[s] = 0ull;
+                if (MODE == 0) {
+                    deg[s] = 0u;
+                } else {
+                    wlo[s] = 0u;
+                    whi[s] = 0u;
+                }
             }
             if (threadIdx.x == 0) nd = 0;
-            uint32_t cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd,
+            uint32_t cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd, g.st,
                                         [&](int slot, uint2 t) {
                                             if (MODE == 0) {
                                                 atomicAdd(&deg[slot], 1u);
@@ -137,26 +194,62 @@ __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
                                             }
                                         });
             // stream S_i past the R chunk
-            stream_pairs(g.Sp, s0, s1, [&](uint2 s) {
-                int slot = tbl_find(keys, mask, s.x, g.seed_slot);
-                if (slot < 0) return;
-                uint32_t dT = timg_deg(g.t, (int32_t)s.y);
-                if (dT == 0) return;
-                if (MODE == 0) acc += (unsigned long long)deg[slot] * dT;
-                else atomicAdd(&w[slot], (unsigned long long)dT);
+            stream_batches(g.Sp, s0, s1, [&](const uint2 (&t)[8], uint32_t n) {
+                int sl[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    sl[k] = (k < (int)n) ? tbl_find(keys, mask, t[k].x, g.seed_slot) : -1;
+                uint32_t dT[8];
+                t_degrees(g.t, tmask, t, sl, n, dT);
+                if (MODE == 0) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (dT[k]) acc += (unsigned long long)deg[sl[k]] * dT[k];
+                } else {
+                    // merge runs of equal B before touching shared memory
+                    int cur = -1;
+                    unsigned long long run = 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (!dT[k]) continue;
+                        if (sl[k] == cur) {
+                            run += dT[k];
+                        } else {
+                            if (cur >= 0) add_u64_split(&wlo[cur], &whi[cur], run);
+                            cur = sl[k];
+                            run = dT[k];
+                        }
+                    }
+                    if (cur >= 0) add_u64_split(&wlo[cur], &whi[cur], run);
+                }
             });
             __syncthreads();
             if (MODE == 1) {
-                // flush: cnt[a] += w[b] for the chunk's R tuples
-                for (uint32_t idx = pos + threadIdx.x; idx < cend; idx += LT) {
-                    uint2 t = __ldg(g.Rp + idx);
-                    int slot = tbl_find(keys, mask, t.y, g.seed_slot);
-                    unsigned long long v = w[slot];
-                    if (v && (uint32_t)t.x < (uint32_t)g.a_domain) {
-                        atomicAdd(g.cnt + t.x, v);
-                        acc += v;
+                // flush: cnt[a] += w[b] for the chunk's R tuples, runs of equal A merged
+                stream_batches(g.Rp, pos, cend, [&](const uint2 (&t)[8], uint32_t n) {
+                    int32_t cur = 0;
+                    unsigned long long run = 0;
+                    bool have = false;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (k >= (int)n) break;
+                        int slot = tbl_find(keys, mask, t[k].y, g.seed_slot);
+                        if (slot < 0) continue;   // only after a recorded insert failure
+                        unsigned long long w =
+                            ((unsigned long long)whi[slot] << 32) | (unsigned long long)wlo[slot];
+                        if (!w || (uint32_t)t[k].x >= (uint32_t)g.a_domain) continue;
+                        if (have && (int32_t)t[k].x == cur) {
+                            run += w;
+                        } else {
+                            if (have) atomicAdd(g.cnt + cur, run);
+                            cur = (int32_t)t[k].x;
+                            run = w;
+                            have = true;
+                        }
+                        acc += w;
                     }
-                }
+                    if (have) atomicAdd(g.cnt + cur, run);
+                });
             }
             __syncthreads();   // the table is rebuilt for the next chunk
             pos = cend;
@@ -197,7 +290,7 @@ __global__ void __launch_bounds__(LT) k_lin_rows(LinArgs g, const unsigned long 
         tbl_clear(keys, cap);
         for (uint32_t s = threadIdx.x; s <= cap; s += LT) deg[s] = 0u;
         if (threadIdx.x == 0) nd = 0;
-        uint32_t cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, max_tuples, &nd,
+        uint32_t cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, max_tuples, &nd, g.st,
                                     [&](int slot, uint2) { atomicAdd(&deg[slot], 1u); });
         // starts of the a-lists: exclusive scan of deg over the slots
         if (threadIdx.x == 0) carry = 0;
@@ -215,7 +308,7 @@ __global__ void __launch_bounds__(LT) k_lin_rows(LinArgs g, const unsigned long 
         for (uint32_t idx = pos + threadIdx.x; idx < cend; idx += LT) {
             uint2 t = __ldg(g.Rp + idx);
             int slot = tbl_find(keys, mask, t.y, g.seed_slot);
-            alist[atomicAdd(&start[slot], 1u)] = (int32_t)t.x;
+            if (slot >= 0) alist[atomicAdd(&start[slot], 1u)] = (int32_t)t.x;
         }
         __syncthreads();
         for (uint32_t s = threadIdx.x; s <= cap; s += LT) start[s] -= deg[s];
@@ -277,7 +370,7 @@ __global__ void k_rows_check(const unsigned long long *base, uint32_t I, long lo
 
 size_t lin_agg_smem(uint32_t cap_log2, int mode) {
     uint32_t cap = 1u << cap_log2;
-    return align256((cap + 1) * 4) + (size_t)(cap + 1) * (mode == 1 ? 8 : 4);
+    return align256((cap + 1) * 4) * (mode == 1 ? 3 : 2);
 }
 
 size_t lin_rows_smem(uint32_t cap_log2, uint32_t max_tuples) {
@@ -292,10 +385,12 @@ cudaError_t lin_agg_launch(const LinArgs &g, int mode, cudaStream_t st) {
     if (mode == 1) {
         e = cudaFuncSetAttribute(k_lin_agg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("lin_probe_groupby", st);
         k_lin_agg<1><<<g.I, LT, smem, st>>>(g);
     } else {
         e = cudaFuncSetAttribute(k_lin_agg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("lin_probe_count", st);
         k_lin_agg<0><<<g.I, LT, smem, st>>>(g);
     }
     return cudaGetLastError();
@@ -304,13 +399,19 @@ cudaError_t lin_agg_launch(const LinArgs &g, int mode, cudaStream_t st) {
 cudaError_t lin_rows_launch(const LinArgs &g, const unsigned long long *base, int32_t *rows,
                             long long capacity, long long *n_rows, uint32_t max_tuples,
                             cudaStream_t st) {
-    k_rows_check<<<1, 1, 0, st>>>(base, g.I, capacity, n_rows, g.st);
+    {
+        ProfScope ps_("rows_check", st);
+        k_rows_check<<<1, 1, 0, st>>>(base, g.I, capacity, n_rows, g.st);
+    }
     if (g.I == 0) return cudaGetLastError();
     size_t smem = lin_rows_smem(g.cap_log2, max_tuples);
     cudaError_t e = cudaFuncSetAttribute(k_lin_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_lin_rows<<<g.I, LT, smem, st>>>(g, base, (int4 *)rows, capacity, max_tuples);
+    {
+        ProfScope ps_("lin_rows", st);
+        k_lin_rows<<<g.I, LT, smem, st>>>(g, base, (int4 *)rows, capacity, max_tuples);
+    }
     return cudaGetLastError();
 }
 

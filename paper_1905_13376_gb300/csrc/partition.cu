@@ -55,8 +55,10 @@ __device__ __forceinline__ Chunk cta_chunk(uint32_t n, uint32_t tiles_per_cta) {
     return c;
 }
 
-// K1: counts[b * G + cta] = number of this CTA's tuples in bucket b.
-template <bool WARP_PRIVATE>
+// K1: counts[b * G + cta] = number of this CTA's tuples in bucket b.  USE
+// says which columns the bucket function reads (1 = x, 2 = y); only those
+// are loaded.
+template <bool WARP_PRIVATE, int USE>
 __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
                                                   const int32_t *__restrict__ y, uint32_t n,
                                                   PartSpec sp, uint32_t tiles_per_cta,
@@ -72,8 +74,9 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
     uint32_t i = c.begin + threadIdx.x * 4;
     if (vec) {
         for (; i + 3 < c.end; i += PT * 4) {
-            int4 xv = __ldg((const int4 *)(x + i));
-            int4 yv = __ldg((const int4 *)(y + i));
+            int4 xv = make_int4(0, 0, 0, 0), yv = make_int4(0, 0, 0, 0);
+            if (USE & 1) xv = __ldg((const int4 *)(x + i));
+            if (USE & 2) yv = __ldg((const int4 *)(y + i));
             atomicAdd(&my[bucket_tuple(xv.x, yv.x, sp)], 1u);
             atomicAdd(&my[bucket_tuple(xv.y, yv.y, sp)], 1u);
             atomicAdd(&my[bucket_tuple(xv.z, yv.z, sp)], 1u);
@@ -81,8 +84,11 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
         }
     }
     for (; i < c.end; i += PT * 4) {
-        for (uint32_t k = i; k < i + 4 && k < c.end; ++k)
-            atomicAdd(&my[bucket_tuple(__ldg(x + k), __ldg(y + k), sp)], 1u);
+        for (uint32_t k = i; k < i + 4 && k < c.end; ++k) {
+            int32_t xv = (USE & 1) ? __ldg(x + k) : 0;
+            int32_t yv = (USE & 2) ? __ldg(y + k) : 0;
+            atomicAdd(&my[bucket_tuple(xv, yv, sp)], 1u);
+        }
     }
     __syncthreads();
     const uint32_t G = gridDim.x;
@@ -96,6 +102,20 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
         }
         counts[(size_t)b * G + blockIdx.x] = s;
     }
+}
+
+template <bool WP>
+cudaError_t hist_launch(const int32_t *x, const int32_t *y, uint32_t n, const PartSpec &sp,
+                        uint32_t G, uint32_t tpc, uint32_t *counts, size_t hs, cudaStream_t st) {
+    int use = (sp.col1 ? 2 : 1) | (sp.col2 < 0 ? 0 : (sp.col2 ? 2 : 1));
+    auto kern = use == 1 ? k_part_hist<WP, 1> : (use == 2 ? k_part_hist<WP, 2> : k_part_hist<WP, 3>);
+    if (hs > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+        if (e != cudaSuccess) return e;
+    }
+    ProfScope ps_("part_hist", st);
+    kern<<<G, PT, hs, st>>>(x, y, n, sp, tpc, counts);
+    return cudaGetLastError();
 }
 
 // bucket_off[b] = scanned[b * G], bucket_off[P] = n.
@@ -268,6 +288,7 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("part_scatter", st);
         kern<<<g.G, PT, smem, st>>>(x, y, n, sp, g.tiles_per_cta, scanned, (T *)out);
     } else {
         size_t smem = P * sizeof(uint32_t);
@@ -275,6 +296,7 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("part_scatter_direct", st);
         kern<<<g.G, PT, smem, st>>>(x, y, n, sp, g.tiles_per_cta, scanned, (T *)out);
     }
     return cudaGetLastError();
@@ -305,19 +327,21 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
 
     const bool warp_private = hist_smem(P, true) <= 48 * 1024;
     size_t hs = hist_smem(P, warp_private);
-    cudaError_t e;
-    if (warp_private) {
-        k_part_hist<true><<<g.G, PT, hs, st>>>(x, y, n, sp, g.tiles_per_cta, counts);
-    } else {
-        e = cudaFuncSetAttribute(k_part_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)hs);
-        if (e != cudaSuccess) return e;
-        k_part_hist<false><<<g.G, PT, hs, st>>>(x, y, n, sp, g.tiles_per_cta, counts);
+    cudaError_t e = warp_private ? hist_launch<true>(x, y, n, sp, g.G, g.tiles_per_cta, counts, hs, st)
+                                 : hist_launch<false>(x, y, n, sp, g.G, g.tiles_per_cta, counts, hs, st);
+    if (e != cudaSuccess) return e;
+    if ((e = scan_excl_u32(counts, ncnt, scan_tmp, st)) != cudaSuccess) return e;
+    {
+        ProfScope ps_("part_offsets", st);
+        k_bucket_offsets<<<(P + 1 + 255) / 256, 256, 0, st>>>(counts, P, g.G, n, bucket_off);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = scan_excl_u32(counts, ncnt, scan_tmp, st)) != cudaSuccess) return e;
-    k_bucket_offsets<<<(P + 1 + 255) / 256, 256, 0, st>>>(counts, P, g.G, n, bucket_off);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // a column that neither the bucket function nor the payload reads is
+    // aliased to the other one, so the scatter's loads of it hit the same lines
+    const bool need_x = sp.col1 == 0 || sp.col2 == 0 || payload == PAY_PAIR || payload == PAY_X;
+    const bool need_y = sp.col1 == 1 || sp.col2 == 1 || payload == PAY_PAIR || payload == PAY_Y;
+    if (!need_y) y = x;
+    if (!need_x) x = y;
     switch (payload) {
         case PAY_PAIR: return scatter_launch<PAY_PAIR>(x, y, n, sp, g, counts, out, st);
         case PAY_X: return scatter_launch<PAY_X>(x, y, n, sp, g, counts, out, st);

@@ -114,9 +114,18 @@ cudaError_t scan_impl(const T *in, T *out, size_t n, bool with_total, void *scra
     }
     size_t tiles = (n + SC_TILE - 1) / SC_TILE;
     T *sums = (T *)scratch;
-    k_tile_sums<T><<<(unsigned)tiles, SC_THREADS, 0, st>>>(in, n, sums);
-    k_scan_sums<T><<<1, SC_THREADS, 0, st>>>(sums, tiles);
-    k_tile_scan<T><<<(unsigned)tiles, SC_THREADS, 0, st>>>(in, out, n, sums, with_total);
+    {
+        ProfScope ps_("scan_tile_sums", st);
+        k_tile_sums<T><<<(unsigned)tiles, SC_THREADS, 0, st>>>(in, n, sums);
+    }
+    {
+        ProfScope ps_("scan_sums", st);
+        k_scan_sums<T><<<1, SC_THREADS, 0, st>>>(sums, tiles);
+    }
+    {
+        ProfScope ps_("scan_tiles", st);
+        k_tile_scan<T><<<(unsigned)tiles, SC_THREADS, 0, st>>>(in, out, n, sums, with_total);
+    }
     return cudaGetLastError();
 }
 

@@ -1,18 +1,24 @@
-// tables.cu -- per-bucket hash-table images of a partitioned relation (K4).
+// tables.cu -- hash tables of T's C values (K4).
 //
-// After T is partitioned by g(C) (Algorithm 1, step 1) every bucket T_j is
-// aggregated into an open-addressing table image: key c -> deg_T(c) (the
-// number of T tuples with that c), and for row output additionally the
-// start of c's group in a D-list.  Bucket j's image occupies slots
-// [2*off[j], 2*off[j] + cap[j]) of one image array, with cap[j] = 2 x the
-// bucket's distinct keys (fill 1/2), so images are 16-byte aligned and can be
-// copied into shared memory with one bulk copy.  The probe kernels hold these
-// images on chip (in shared memory, or in L2 when T stays whole).
+// After T is partitioned by g(C) (Algorithm 1, step 1) the probe needs, for
+// each c, deg_T(c) = |{(c,d) in T}| (count modes) or c's group of D values
+// (row output).  Two layouts:
 //
-// A bucket is first aggregated in a shared-memory table (one CTA per
-// bucket); a bucket with more tuples than that table can hold is aggregated
-// directly in its global region instead (capacity 2 x its tuples), which
-// keeps every input exact whatever its skew.
+//  * one table ("T held whole on chip", used when S is not split by C):
+//    every bucket T_j is aggregated in shared memory (one CTA per bucket,
+//    32-bit atomics), its (c, count) entries are appended to a compact list,
+//    and the entries are then inserted into a single open-addressing table of
+//    2^k >= 2 x (entries) packed (count << 32 | c) slots that stays resident
+//    in L2.  A probe is one 8-byte load in the common case.
+//  * bucket images (S split by (H(B), g(C)), and row output): bucket j's
+//    table occupies slots [2*off[j], 2*off[j] + cap[j]) of one image array,
+//    cap[j] = 2 x its distinct keys, 16-byte aligned so that it can be copied
+//    into shared memory in one bulk copy.  With row output a parallel start[]
+//    array gives the first position of c's D values in dlist.
+//
+// A bucket whose distinct keys overflow the shared-memory table is handled
+// in pieces (the table is flushed and restarted), and the global insert adds
+// the partial counts together, so any skew stays exact.
 #include "internal.h"
 #include "tables.h"
 
@@ -20,33 +26,16 @@ namespace mwj {
 namespace {
 
 constexpr int BT = 512;
-constexpr uint32_t kSmemSlots = 8192;   // 64 KB of packed slots
+constexpr uint32_t kAggSlots = 8192;          // shared-memory aggregation table
+constexpr uint32_t kImgSmemSlots = 8192;      // 64 KB of packed slots (bucket images)
 
-__device__ __forceinline__ void agg_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
-                                           uint32_t seed) {
-    uint32_t s = mix32(k ^ seed) & mask;
-    const unsigned long long fresh = (1ull << 32) | (unsigned long long)k;
-    for (;;) {
-        unsigned long long v = tbl[s];
-        if (v == kEmpty64) {
-            unsigned long long old = atomicCAS(&tbl[s], kEmpty64, fresh);
-            if (old == kEmpty64) return;
-            v = old;
-        }
-        if ((uint32_t)v == k) {
-            atomicAdd(&tbl[s], 1ull << 32);
-            return;
-        }
-        s = (s + 1) & mask;
-    }
-}
-
-// insert into a global region of arbitrary capacity (fastrange start)
+// insert into a global region of arbitrary capacity (fastrange start), adding `add`
 __device__ __forceinline__ uint32_t gagg_insert(unsigned long long *tbl, uint32_t cap, uint32_t k,
-                                                uint32_t seed, unsigned long long add) {
+                                                uint32_t seed, unsigned long long add,
+                                                DevStatus *st) {
     uint32_t s = fastrange(mix32(k ^ seed), cap);
     const unsigned long long fresh = (add << 32) | (unsigned long long)k;
-    for (;;) {
+    for (uint32_t it = 0; it < cap; ++it) {
         unsigned long long v = tbl[s];
         if (v == kEmpty64) {
             unsigned long long old = atomicCAS(&tbl[s], kEmpty64, fresh);
@@ -58,6 +47,158 @@ __device__ __forceinline__ uint32_t gagg_insert(unsigned long long *tbl, uint32_
             return s;
         }
         s = (s + 1 == cap) ? 0 : s + 1;
+    }
+    set_status(st, MWJ_ERR_CHECK, 2);   // sized to stay half empty: cannot happen
+    return 0;
+}
+
+// insert into the power-of-two single table
+__device__ __forceinline__ void single_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
+                                              uint32_t seed, unsigned long long add,
+                                              DevStatus *st) {
+    uint32_t s = mix32(k ^ seed) & mask;
+    const unsigned long long fresh = (add << 32) | (unsigned long long)k;
+    for (uint32_t it = 0; it <= mask; ++it) {
+        unsigned long long v = tbl[s];
+        if (v == kEmpty64) {
+            unsigned long long old = atomicCAS(&tbl[s], kEmpty64, fresh);
+            if (old == kEmpty64) return;
+            v = old;
+        }
+        if ((uint32_t)v == k) {
+            atomicAdd(&tbl[s], add << 32);
+            return;
+        }
+        s = (s + 1) & mask;
+    }
+    set_status(st, MWJ_ERR_CHECK, 3);
+}
+
+// ---------------------------------------------------------------------------
+// single table
+// ---------------------------------------------------------------------------
+
+// One CTA per bucket: aggregate the bucket's keys in shared memory and append
+// (key, count) entries to ekey/ecnt at the bucket's tuple offset.
+__global__ void __launch_bounds__(BT) k_tagg(const uint32_t *__restrict__ keys,
+                                             const uint32_t *__restrict__ off, uint32_t J,
+                                             uint32_t seed, uint32_t *__restrict__ ekey,
+                                             uint32_t *__restrict__ ecnt,
+                                             uint32_t *__restrict__ ecount, DevStatus *st) {
+    extern __shared__ uint32_t sm[];
+    uint32_t *tk = sm;                         // kAggSlots + 1 keys
+    uint32_t *tc = sm + kAggSlots + 1;         // kAggSlots + 1 counts
+    __shared__ uint32_t nd, nout;
+    const uint32_t mask = kAggSlots - 1;
+    for (uint32_t j = blockIdx.x; j < J; j += gridDim.x) {
+        const uint32_t o0 = off[j], o1 = off[j + 1];
+        if (threadIdx.x == 0) nout = 0;
+        uint32_t pos = o0;
+        while (pos < o1) {
+            for (uint32_t s = threadIdx.x; s <= kAggSlots; s += BT) {
+                tk[s] = (s < kAggSlots) ? kEmptyKey : 0u;
+                tc[s] = 0u;
+            }
+            if (threadIdx.x == 0) nd = 0;
+            // rounds of rt keys while the table stays at most 3/4 full
+            const uint32_t rt = round_tuples(kAggSlots, 4 * BT);
+            for (;;) {
+                __syncthreads();
+                const uint32_t filled = nd;
+                __syncthreads();
+                if (pos >= o1 || filled + rt > kAggSlots - kAggSlots / 4) break;
+                uint32_t fresh_n = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t li = threadIdx.x + k * BT;
+                    uint32_t i = pos + li;
+                    if (li < rt && i < o1) {
+                        bool fresh;
+                        int s = tbl_insert(tk, mask, __ldg(keys + i), seed, &fresh);
+                        if (s < 0) {
+                            set_status(st, MWJ_ERR_CHECK, 4);
+                            continue;
+                        }
+                        fresh_n += fresh;
+                        atomicAdd(&tc[s], 1u);
+                    }
+                }
+                fresh_n = warp_sum(fresh_n);
+                if ((threadIdx.x & 31) == 0 && fresh_n) atomicAdd(&nd, fresh_n);
+                pos += rt;
+            }
+            // flush the table's entries
+            for (uint32_t s = threadIdx.x; s <= kAggSlots; s += BT) {
+                uint32_t c = tc[s];
+                if (c) {
+                    uint32_t k = (s < kAggSlots) ? tk[s] : kEmptyKey;
+                    uint32_t p = atomicAdd(&nout, 1u);
+                    ekey[o0 + p] = k;
+                    ecnt[o0 + p] = c;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) ecount[j] = nout;
+        __syncthreads();
+    }
+}
+
+// Sum of the entry counts (one CTA) and the table's power-of-two mask.
+__global__ void k_tsize(const uint32_t *__restrict__ ecount, uint32_t J, uint32_t *__restrict__ meta) {
+    __shared__ unsigned long long red[32];
+    unsigned long long s = 0;
+    for (uint32_t j = threadIdx.x; j < J; j += blockDim.x) s += ecount[j];
+    s = block_sum_u64(s, red);
+    if (threadIdx.x == 0) {
+        unsigned long long cap = 16;
+        while (cap < 2 * s) cap <<= 1;
+        meta[0] = (uint32_t)(cap - 1);   // mask
+        meta[1] = (uint32_t)s;
+    }
+}
+
+__global__ void k_tclear(unsigned long long *__restrict__ tbl, const uint32_t *__restrict__ meta) {
+    const uint64_t cap = (uint64_t)meta[0] + 1;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < cap;
+         s += (uint64_t)gridDim.x * blockDim.x)
+        tbl[s] = kEmpty64;
+}
+
+__global__ void __launch_bounds__(BT) k_tinsert(const uint32_t *__restrict__ ekey,
+                                                const uint32_t *__restrict__ ecnt,
+                                                const uint32_t *__restrict__ off,
+                                                const uint32_t *__restrict__ ecount, uint32_t J,
+                                                uint32_t seed, unsigned long long *__restrict__ tbl,
+                                                const uint32_t *__restrict__ meta, DevStatus *st) {
+    const uint32_t mask = meta[0];
+    for (uint32_t j = blockIdx.x; j < J; j += gridDim.x) {
+        const uint32_t o0 = off[j], e = ecount[j];
+        for (uint32_t i = threadIdx.x; i < e; i += BT)
+            single_insert(tbl, mask, ekey[o0 + i], seed, ecnt[o0 + i], st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bucket images
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void img_agg_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
+                                               uint32_t seed) {
+    uint32_t s = mix32(k ^ seed) & mask;
+    const unsigned long long fresh = (1ull << 32) | (unsigned long long)k;
+    for (uint32_t it = 0; it <= mask; ++it) {   // sized >= 2x the bucket: never full
+        unsigned long long v = tbl[s];
+        if (v == kEmpty64) {
+            unsigned long long old = atomicCAS(&tbl[s], kEmpty64, fresh);
+            if (old == kEmpty64) return;
+            v = old;
+        }
+        if ((uint32_t)v == k) {
+            atomicAdd(&tbl[s], 1ull << 32);
+            return;
+        }
+        s = (s + 1) & mask;
     }
 }
 
@@ -73,8 +214,8 @@ __global__ void __launch_bounds__(BT) k_tbuild(const uint32_t *__restrict__ keys
                                                uint32_t seed, unsigned long long *__restrict__ img,
                                                uint32_t *__restrict__ capv,
                                                uint32_t *__restrict__ startv,
-                                               int32_t *__restrict__ dlist) {
-    extern __shared__ unsigned long long tbl[];   // kSmemSlots
+                                               int32_t *__restrict__ dlist, DevStatus *st) {
+    extern __shared__ unsigned long long tbl[];   // kImgSmemSlots
     __shared__ unsigned long long red[32];
     for (uint32_t j = blockIdx.x; j < J; j += gridDim.x) {
         const uint32_t o0 = off[j], o1 = off[j + 1];
@@ -85,14 +226,14 @@ __global__ void __launch_bounds__(BT) k_tbuild(const uint32_t *__restrict__ keys
             if (threadIdx.x == 0) capv[j] = 0;
             continue;
         }
-        if (2u * n <= kSmemSlots) {
+        if (2u * n <= kImgSmemSlots) {
             uint32_t sc = 16;
             while (sc < 2u * n) sc <<= 1;
             const uint32_t mask = sc - 1;
             for (uint32_t s = threadIdx.x; s < sc; s += BT) tbl[s] = kEmpty64;
             __syncthreads();
             for (uint32_t i = o0 + threadIdx.x; i < o1; i += BT)
-                agg_insert(tbl, mask, key_of(keys, pairs, i), seed);
+                img_agg_insert(tbl, mask, key_of(keys, pairs, i), seed);
             __syncthreads();
             unsigned long long mine = 0;
             for (uint32_t s = threadIdx.x; s < sc; s += BT) mine += (tbl[s] != kEmpty64);
@@ -102,14 +243,14 @@ __global__ void __launch_bounds__(BT) k_tbuild(const uint32_t *__restrict__ keys
             __syncthreads();
             for (uint32_t s = threadIdx.x; s < sc; s += BT) {
                 unsigned long long v = tbl[s];
-                if (v != kEmpty64) gagg_insert(reg, cap, (uint32_t)v, seed, v >> 32);
+                if (v != kEmpty64) gagg_insert(reg, cap, (uint32_t)v, seed, v >> 32, st);
             }
         } else {
             cap = 2u * n;
             for (uint32_t s = threadIdx.x; s < cap; s += BT) reg[s] = kEmpty64;
             __syncthreads();
             for (uint32_t i = o0 + threadIdx.x; i < o1; i += BT)
-                gagg_insert(reg, cap, key_of(keys, pairs, i), seed, 1ull);
+                gagg_insert(reg, cap, key_of(keys, pairs, i), seed, 1ull, st);
         }
         if (threadIdx.x == 0) capv[j] = cap;
         __syncthreads();
@@ -136,13 +277,19 @@ __global__ void __launch_bounds__(BT) k_tbuild(const uint32_t *__restrict__ keys
                 uint2 t = pairs[i];
                 // plain loads: the image was written earlier in this kernel
                 uint32_t s = fastrange(mix32(t.x ^ seed), cap);
-                for (;;) {
+                bool found = false;
+                for (uint32_t it = 0; it < cap; ++it) {
                     unsigned long long v = reg[s];
-                    if (v != kEmpty64 && (uint32_t)v == t.x) break;
+                    if (v != kEmpty64 && (uint32_t)v == t.x) { found = true; break; }
                     s = (s + 1 == cap) ? 0 : s + 1;
                 }
+                if (!found) {
+                    set_status(st, MWJ_ERR_CHECK, 5);
+                    continue;
+                }
                 uint32_t p = atomicAdd(&sv[s], 1u);
-                dlist[p] = (int32_t)t.y;
+                if (p >= o0 && p < o1) dlist[p] = (int32_t)t.y;
+                else set_status(st, MWJ_ERR_CHECK, 6);
             }
             __syncthreads();
             for (uint32_t s = threadIdx.x; s < cap; s += BT) {
@@ -156,23 +303,61 @@ __global__ void __launch_bounds__(BT) k_tbuild(const uint32_t *__restrict__ keys
 
 }  // namespace
 
+size_t single_table_slots(int64_t nT) {
+    uint64_t cap = 16;
+    while (cap < 2 * (uint64_t)(nT > 0 ? nT : 1)) cap <<= 1;
+    return cap;
+}
+
+cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32_t J, uint32_t seed,
+                               uint32_t *ekey, uint32_t *ecnt, uint32_t *ecount, uint32_t *meta,
+                               uint64_t *tbl, DevStatus *status, int num_sms, cudaStream_t st) {
+    unsigned grid = J < (uint32_t)num_sms * 4 ? J : (unsigned)num_sms * 4;
+    if (grid == 0) grid = 1;
+    const size_t smem = 2 * (kAggSlots + 1) * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_tagg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (J > 0) {
+        ProfScope ps_("t_aggregate", st);
+        k_tagg<<<grid, BT, smem, st>>>(keys, off, J, seed, ekey, ecnt, ecount, status);
+    }
+    {
+        ProfScope ps_("t_size", st);
+        k_tsize<<<1, 1024, 0, st>>>(ecount, J, meta);
+    }
+    {
+        ProfScope ps_("t_clear", st);
+        k_tclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)tbl, meta);
+    }
+    if (J > 0) {
+        ProfScope ps_("t_insert", st);
+        k_tinsert<<<grid, BT, 0, st>>>(ekey, ecnt, off, ecount, J, seed, (unsigned long long *)tbl,
+                                       meta, status);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t tables_build(const uint32_t *keys, const uint2 *pairs, const uint32_t *off, uint32_t J,
                          uint32_t seed, uint64_t *img, uint32_t *capv, uint32_t *startv,
-                         int32_t *dlist, int num_sms, cudaStream_t st) {
+                         int32_t *dlist, DevStatus *status, int num_sms, cudaStream_t st) {
     if (J == 0) return cudaSuccess;
     unsigned grid = J < (uint32_t)num_sms * 8 ? J : (unsigned)num_sms * 8;
-    const size_t smem = kSmemSlots * sizeof(unsigned long long);
+    const size_t smem = kImgSmemSlots * sizeof(unsigned long long);
     cudaError_t e;
     if (startv) {
         e = cudaFuncSetAttribute(k_tbuild<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("table_build_csr", st);
         k_tbuild<true><<<grid, BT, smem, st>>>(keys, pairs, off, J, seed,
-                                               (unsigned long long *)img, capv, startv, dlist);
+                                               (unsigned long long *)img, capv, startv, dlist,
+                                               status);
     } else {
         e = cudaFuncSetAttribute(k_tbuild<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfScope ps_("table_build", st);
         k_tbuild<false><<<grid, BT, smem, st>>>(keys, pairs, off, J, seed,
-                                                (unsigned long long *)img, capv, nullptr, nullptr);
+                                                (unsigned long long *)img, capv, nullptr, nullptr,
+                                                status);
     }
     return cudaGetLastError();
 }

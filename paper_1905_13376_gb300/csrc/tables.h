@@ -1,32 +1,45 @@
-// tables.h -- bucket table images of a partitioned relation and their lookup.
+// tables.h -- T's tables (one L2-resident table, or per-bucket images) and their lookup.
 #pragma once
 
 #include "common.cuh"
 
 namespace mwj {
 
-// Images of T's g(C) buckets: bucket j = bucket_of(c, seed_bucket, J) lives
-// at img[2*off[j] .. 2*off[j] + cap[j]) as packed (deg << 32 | c) slots.  With
-// row output, start[2*off[j] + slot] is the first position of c's D values in
-// dlist (dlist is grouped by bucket, then by key).
+// J == 0: one table of (meta[0] + 1) packed (deg << 32 | c) slots, slot hash
+//         mix32(c ^ seed_slot) & meta[0].
+// J >= 1: bucket j = bucket_of(c, seed_bucket, J) lives at
+//         img[2*off[j] .. 2*off[j] + cap[j]); with row output start[2*off[j] + slot]
+//         is the first position of c's D values in dlist.
 struct TImg {
     const uint64_t *img;
     const uint32_t *off;
     const uint32_t *cap;
     const uint32_t *start;
     const int32_t *dlist;
+    const uint32_t *meta;
     uint32_t J;
     uint32_t seed_bucket;
     uint32_t seed_slot;
 };
 
 __device__ __forceinline__ uint32_t timg_deg(const TImg &t, int32_t c) {
+    if (t.J == 0) {
+        const uint32_t mask = __ldg(t.meta);
+        uint32_t s = mix32((uint32_t)c ^ t.seed_slot) & mask;
+        for (uint32_t it = 0; it <= mask; ++it) {
+            uint64_t v = __ldg((const unsigned long long *)(t.img + s));
+            if (v == kEmpty64) return 0;
+            if ((uint32_t)v == (uint32_t)c) return (uint32_t)(v >> 32);
+            s = (s + 1) & mask;
+        }
+        return 0;
+    }
     uint32_t j = (t.J == 1) ? 0u : bucket_of(c, t.seed_bucket, t.J);
     uint64_t base = 2ull * __ldg(t.off + j);
     return img_lookup(t.img + base, __ldg(t.cap + j), (uint32_t)c, t.seed_slot);
 }
 
-// deg and start of c (deg 0 when absent)
+// deg and start of c (deg 0 when absent); bucket images only
 __device__ __forceinline__ uint32_t timg_deg_start(const TImg &t, int32_t c, uint32_t *start) {
     uint32_t j = (t.J == 1) ? 0u : bucket_of(c, t.seed_bucket, t.J);
     uint64_t base = 2ull * __ldg(t.off + j);
@@ -39,6 +52,13 @@ __device__ __forceinline__ uint32_t timg_deg_start(const TImg &t, int32_t c, uin
 
 cudaError_t tables_build(const uint32_t *keys, const uint2 *pairs, const uint32_t *off, uint32_t J,
                          uint32_t seed, uint64_t *img, uint32_t *capv, uint32_t *startv,
-                         int32_t *dlist, int num_sms, cudaStream_t st);
+                         int32_t *dlist, DevStatus *status, int num_sms, cudaStream_t st);
+
+// slots to reserve for the single table of nT tuples (worst case)
+size_t single_table_slots(int64_t nT);
+// ekey/ecnt: nT entries each; ecount: J; meta: 2.
+cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32_t J, uint32_t seed,
+                               uint32_t *ekey, uint32_t *ecnt, uint32_t *ecount, uint32_t *meta,
+                               uint64_t *tbl, DevStatus *status, int num_sms, cudaStream_t st);
 
 }  // namespace mwj
