@@ -74,15 +74,65 @@ __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, ui
     return cend < r1 ? cend : r1;
 }
 
-// Tuples p[s0, s1) in batches of up to 8 consecutive tuples per thread
-// (thread t takes [b + 8t, b + 8t + 8) of every 8*LT-tuple round), loaded with
-// 128-bit loads; f(t, n) gets the batch and its length.
+// One optimistic pass: insert every R tuple of [pos, r1) with probe sequences
+// of at most 32 slots.  Succeeds when no insert failed and the table ended at
+// most 3/4 full; otherwise the caller clears the table and builds in rounds.
+// Ends with a barrier.
+template <typename F>
+__device__ __forceinline__ bool build_all(const uint2 *__restrict__ Rp, uint32_t pos, uint32_t r1,
+                                          uint32_t *keys, uint32_t cap, uint32_t seed,
+                                          uint32_t *nd, uint32_t *bad, F &&on_insert) {
+    const uint32_t mask = cap - 1;
+    uint32_t fresh_n = 0;
+    bool failed = false;
+    for (uint32_t idx = pos + threadIdx.x; idx < r1; idx += LT) {
+        uint2 t = __ldg(Rp + idx);
+        int slot;
+        bool fresh = false;
+        if (t.y == kEmptyKey) {
+            slot = tbl_insert(keys, mask, t.y, seed, &fresh);
+        } else {
+            slot = -1;
+            uint32_t s = mix32(t.y ^ seed) & mask;
+            for (int it = 0; it < 32; ++it) {
+                uint32_t q = keys[s];
+                if (q == t.y) { slot = (int)s; break; }
+                if (q == kEmptyKey) {
+                    uint32_t old = atomicCAS(&keys[s], kEmptyKey, t.y);
+                    if (old == kEmptyKey) { slot = (int)s; fresh = true; break; }
+                    if (old == t.y) { slot = (int)s; break; }
+                }
+                s = (s + 1) & mask;
+            }
+        }
+        if (slot < 0) {
+            failed = true;
+            break;
+        }
+        fresh_n += fresh;
+        on_insert(slot, t);
+    }
+    fresh_n = warp_sum(fresh_n);
+    unsigned anyfail = __ballot_sync(0xffffffffu, failed);
+    if ((threadIdx.x & 31) == 0) {
+        if (fresh_n) atomicAdd(nd, fresh_n);
+        if (anyfail) atomicOr(bad, 1u);
+    }
+    __syncthreads();
+    return !(*bad) && *nd <= cap - cap / 4;
+}
+
+constexpr int NB = 4;   // tuples per thread per batch
+
+// Tuples p[s0, s1) in batches of up to NB consecutive tuples per thread
+// (thread t takes [b + NB t, b + NB (t+1)) of every NB*LT-tuple round), loaded
+// with 128-bit loads; f(t, n) gets the batch and its length.
 template <typename F>
 __device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint32_t s0, uint32_t s1,
                                                F &&f) {
     if (s0 >= s1) return;
     uint32_t a = s0;
-    uint2 t[8];
+    uint2 t[NB];
     if (a & 1u) {
         if (threadIdx.x == 0) {
             t[0] = __ldg(p + a);
@@ -90,42 +140,42 @@ __device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint
         }
         ++a;
     }
-    for (uint32_t b = a + 8 * threadIdx.x; b < s1; b += 8 * LT) {
-        const uint32_t n = min(8u, s1 - b);
-        if (n == 8) {
+    for (uint32_t b = a + NB * threadIdx.x; b < s1; b += NB * LT) {
+        const uint32_t n = min((uint32_t)NB, s1 - b);
+        if (n == NB) {
             const uint4 *q = (const uint4 *)(p + b);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < NB / 2; ++k) {
                 uint4 u = __ldg(q + k);
                 t[2 * k] = make_uint2(u.x, u.y);
                 t[2 * k + 1] = make_uint2(u.z, u.w);
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < NB; ++k)
                 if (k < (int)n) t[k] = __ldg(p + b + k);
         }
         f(t, n);
     }
 }
 
-// deg_T of the 8 C values of a batch: the first probe of every tuple is
+// deg_T of the NB C values of a batch: the first probe of every tuple is
 // issued before any is consumed (one L2 round trip for the whole batch in
 // the common case).
-__device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const uint2 (&t)[8],
-                                          const int (&sl)[8], uint32_t n, uint32_t (&dT)[8]) {
+__device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const uint2 (&t)[NB],
+                                          const int (&sl)[NB], uint32_t n, uint32_t (&dT)[NB]) {
     if (T.J == 0) {
-        uint32_t ts[8];
-        unsigned long long v[8];
+        uint32_t ts[NB];
+        unsigned long long v[NB];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < NB; ++k) {
             if (k < (int)n && sl[k] >= 0) {
                 ts[k] = mix32(t[k].y ^ T.seed_slot) & tmask;
                 v[k] = __ldg((const unsigned long long *)(T.img + ts[k]));
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < NB; ++k) {
             dT[k] = 0;
             if (k < (int)n && sl[k] >= 0) {
                 unsigned long long x = v[k];
@@ -140,7 +190,7 @@ __device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const u
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < NB; ++k)
             dT[k] = (k < (int)n && sl[k] >= 0) ? timg_deg(T, (int32_t)t[k].y) : 0u;
     }
 }
@@ -155,7 +205,7 @@ __device__ __forceinline__ void add_u64_split(uint32_t *lo, uint32_t *hi, unsign
 
 // COUNT (MODE 0) and GROUP BY A (MODE 1).  One CTA per R bucket.
 template <int MODE>
-__global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
+__global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t cap = 1u << g.cap_log2;
     const size_t arr = align256((cap + 1) * sizeof(uint32_t));
@@ -163,7 +213,7 @@ __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
     uint32_t *deg = (uint32_t *)(smem + arr);          // MODE 0
     uint32_t *wlo = (uint32_t *)(smem + arr);          // MODE 1
     uint32_t *whi = (uint32_t *)(smem + 2 * arr);      // MODE 1
-    __shared__ uint32_t nd;
+    __shared__ uint32_t nd, bad;
     __shared__ unsigned long long red[32];
 
     const uint32_t i = blockIdx.x;
@@ -184,33 +234,56 @@ __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
                     whi[s] = 0u;
                 }
             }
-            if (threadIdx.x == 0) nd = 0;
-            uint32_t cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd, g.st,
-                                        [&](int slot, uint2 t) {
-                                            if (MODE == 0) {
-                                                atomicAdd(&deg[slot], 1u);
-                                            } else if ((uint32_t)t.x >= (uint32_t)g.a_domain) {
-                                                set_status(g.st, MWJ_ERR_DOMAIN, (int32_t)t.x);
-                                            }
-                                        });
+            if (threadIdx.x == 0) {
+                nd = 0;
+                bad = 0;
+            }
+            auto on_insert = [&](int slot, uint2 t) {
+                if (MODE == 0) {
+                    atomicAdd(&deg[slot], 1u);
+                } else if ((uint32_t)t.x >= (uint32_t)g.a_domain) {
+                    set_status(g.st, MWJ_ERR_DOMAIN, (int32_t)t.x);
+                }
+            };
+            uint32_t cend;
+            __syncthreads();
+            if (pos == r0 && build_all(g.Rp, pos, r1, keys, cap, g.seed_slot, &nd, &bad, on_insert)) {
+                cend = r1;
+            } else {
+                if (pos == r0) {   // the optimistic pass overflowed: start over in rounds
+                    tbl_clear(keys, cap);
+                    for (uint32_t s = threadIdx.x; s <= cap; s += LT) {
+                        if (MODE == 0) {
+                            deg[s] = 0u;
+                        } else {
+                            wlo[s] = 0u;
+                            whi[s] = 0u;
+                        }
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) nd = 0;
+                }
+                cend = build_chunk(g.Rp, pos, r1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd, g.st,
+                                   on_insert);
+            }
             // stream S_i past the R chunk
-            stream_batches(g.Sp, s0, s1, [&](const uint2 (&t)[8], uint32_t n) {
-                int sl[8];
+            stream_batches(g.Sp, s0, s1, [&](const uint2 (&t)[NB], uint32_t n) {
+                int sl[NB];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
+                for (int k = 0; k < NB; ++k)
                     sl[k] = (k < (int)n) ? tbl_find(keys, mask, t[k].x, g.seed_slot) : -1;
-                uint32_t dT[8];
+                uint32_t dT[NB];
                 t_degrees(g.t, tmask, t, sl, n, dT);
                 if (MODE == 0) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
+                    for (int k = 0; k < NB; ++k)
                         if (dT[k]) acc += (unsigned long long)deg[sl[k]] * dT[k];
                 } else {
                     // merge runs of equal B before touching shared memory
                     int cur = -1;
                     unsigned long long run = 0;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < NB; ++k) {
                         if (!dT[k]) continue;
                         if (sl[k] == cur) {
                             run += dT[k];
@@ -226,12 +299,12 @@ __global__ void __launch_bounds__(LT) k_lin_agg(LinArgs g) {
             __syncthreads();
             if (MODE == 1) {
                 // flush: cnt[a] += w[b] for the chunk's R tuples, runs of equal A merged
-                stream_batches(g.Rp, pos, cend, [&](const uint2 (&t)[8], uint32_t n) {
+                stream_batches(g.Rp, pos, cend, [&](const uint2 (&t)[NB], uint32_t n) {
                     int32_t cur = 0;
                     unsigned long long run = 0;
                     bool have = false;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < NB; ++k) {
                         if (k >= (int)n) break;
                         int slot = tbl_find(keys, mask, t[k].y, g.seed_slot);
                         if (slot < 0) continue;   // only after a recorded insert failure

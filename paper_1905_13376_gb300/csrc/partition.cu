@@ -263,10 +263,12 @@ struct Geometry {
     uint32_t G, tiles_per_cta;
 };
 
-Geometry geometry(int64_t n, int num_sms) {
+// G CTAs (at most max_ctas, one resident wave) each own a contiguous run of
+// tiles_per_cta tiles.
+Geometry geometry(int64_t n, int max_ctas) {
     uint64_t tiles = ((uint64_t)n + TILE - 1) / TILE;
     if (tiles == 0) tiles = 1;
-    uint64_t gmax = (uint64_t)num_sms * 4;
+    uint64_t gmax = (uint64_t)(max_ctas > 0 ? max_ctas : 1);
     uint64_t G = tiles < gmax ? tiles : gmax;
     uint64_t tpc = (tiles + G - 1) / G;
     G = (tiles + tpc - 1) / tpc;
@@ -305,7 +307,7 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
 }  // namespace
 
 size_t part_scratch_bytes(int64_t n, uint32_t P, int num_sms) {
-    Geometry g = geometry(n, num_sms);
+    Geometry g = geometry(n, num_sms * 4);
     size_t cnt = (size_t)P * g.G;
     return align256(cnt * sizeof(uint32_t)) + scan_scratch_bytes(cnt);
 }
@@ -320,7 +322,23 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     if (n == 0) {
         return cudaMemsetAsync(bucket_off, 0, (P + 1) * sizeof(uint32_t), st);
     }
-    Geometry g = geometry(n64, num_sms);
+    // one wave of the scatter kernel: its resident CTAs per SM x SMs
+    int occ = 1;
+    {
+        const bool staged = P <= kStagedMaxP;
+        size_t ssz = payload == PAY_PAIR ? sizeof(uint2) : sizeof(uint32_t);
+        size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint16_t)
+                             : P * sizeof(uint32_t);
+        const void *kern = staged ? (payload == PAY_PAIR ? (const void *)k_part_scatter_staged<PAY_PAIR>
+                                                         : (const void *)k_part_scatter_staged<PAY_X>)
+                                  : (payload == PAY_PAIR ? (const void *)k_part_scatter_direct<PAY_PAIR>
+                                                         : (const void *)k_part_scatter_direct<PAY_X>);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PT, smem) != cudaSuccess || occ < 1)
+            occ = 1;
+        if (occ > 4) occ = 4;
+    }
+    Geometry g = geometry(n64, num_sms * occ);
     uint32_t *counts = (uint32_t *)scratch;
     size_t ncnt = (size_t)P * g.G;
     void *scan_tmp = (char *)scratch + align256(ncnt * sizeof(uint32_t));
