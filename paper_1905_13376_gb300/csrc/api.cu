@@ -337,6 +337,10 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
     PartSpec pr{1, sd.B, p.I, -1, 0, 1};
+    if (out->mode == MWJ_COUNT_GROUP_BY_A) {   // every a of R must lie in the group-by domain
+        pr.dom = (uint32_t)out->a_domain;
+        pr.st = ctx->status;
+    }
     e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
@@ -389,7 +393,6 @@ mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel
 namespace mwj {
 
 mwj_status check_out(mwj_ctx *ctx, const mwj_out *out, int arity) {
-    (void)arity;
     if (!out->total) return fail(ctx, MWJ_ERR_INVALID_ARG, "out.total is NULL");
     switch (out->mode) {
         case MWJ_COUNT: return MWJ_OK;
@@ -400,8 +403,10 @@ mwj_status check_out(mwj_ctx *ctx, const mwj_out *out, int arity) {
         case MWJ_MATERIALIZE:
             if (!out->n_rows || out->capacity < 0 || (out->capacity > 0 && !out->rows))
                 return fail(ctx, MWJ_ERR_INVALID_ARG, "rows/n_rows/capacity invalid");
-            if (((uintptr_t)out->rows & 15) != 0)
-                return fail(ctx, MWJ_ERR_INVALID_ARG, "rows must be 16-byte aligned");
+            if (arity == 4 && ((uintptr_t)out->rows & 15) != 0)
+                return fail(ctx, MWJ_ERR_INVALID_ARG, "linear rows must be 16-byte aligned");
+            if (((uintptr_t)out->rows & 3) != 0)
+                return fail(ctx, MWJ_ERR_INVALID_ARG, "rows must be 4-byte aligned");
             return MWJ_OK;
         default: return fail(ctx, MWJ_ERR_INVALID_ARG, "bad mode %d", (int)out->mode);
     }

@@ -18,6 +18,8 @@ struct PartSpec {
     uint32_t seed1, P1;
     int col2;
     uint32_t seed2, P2;
+    uint32_t dom = 0;     // when > 0: every x must lie in [0, dom), else MWJ_ERR_DOMAIN
+    DevStatus *st = nullptr;
     __host__ __device__ uint32_t P() const { return P1 * (col2 >= 0 ? P2 : 1u); }
 };
 

@@ -238,12 +238,9 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
                 nd = 0;
                 bad = 0;
             }
-            auto on_insert = [&](int slot, uint2 t) {
-                if (MODE == 0) {
-                    atomicAdd(&deg[slot], 1u);
-                } else if ((uint32_t)t.x >= (uint32_t)g.a_domain) {
-                    set_status(g.st, MWJ_ERR_DOMAIN, (int32_t)t.x);
-                }
+            // (A values were checked against the group-by domain while R was partitioned)
+            auto on_insert = [&](int slot, uint2) {
+                if (MODE == 0) atomicAdd(&deg[slot], 1u);
             };
             uint32_t cend;
             __syncthreads();

@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
             for (int k = 0; k < 4; ++k) {
                 int j = h * 4 + k;
                 if (li + k < tn) {
+                    if (sp.dom && (uint32_t)xs[k] >= sp.dom) set_status(sp.st, MWJ_ERR_DOMAIN, xs[k]);
                     bk[j] = bucket_tuple(xs[k], ys[k], sp);
                     rk[j] = atomicAdd(&cnt[bk[j]], 1u);
                     pv[j] = make_pay<PAY>(xs[k], ys[k]);
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_direct(
     Chunk c = cta_chunk(n, tiles_per_cta);
     for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
         int32_t xv = __ldg(x + i), yv = __ldg(y + i);
+        if (sp.dom && (uint32_t)xv >= sp.dom) set_status(sp.st, MWJ_ERR_DOMAIN, xv);
         uint32_t b = bucket_tuple(xv, yv, sp);
         uint32_t p = atomicAdd(&cur[b], 1u);
         out[p] = make_pay<PAY>(xv, yv);
@@ -356,7 +358,8 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // a column that neither the bucket function nor the payload reads is
     // aliased to the other one, so the scatter's loads of it hit the same lines
-    const bool need_x = sp.col1 == 0 || sp.col2 == 0 || payload == PAY_PAIR || payload == PAY_X;
+    const bool need_x = sp.col1 == 0 || sp.col2 == 0 || payload == PAY_PAIR || payload == PAY_X ||
+                        sp.dom > 0;
     const bool need_y = sp.col1 == 1 || sp.col2 == 1 || payload == PAY_PAIR || payload == PAY_Y;
     if (!need_y) y = x;
     if (!need_x) x = y;

@@ -1,0 +1,151 @@
+"""Parity of the cyclic 3-way (triangle) join, CUDA through the C ABI, with the oracle."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_13376_gb300 import binding, datagen
+
+from gpu_util import cu, sorted_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.set_device(0)
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def check_all_modes(ctx, R, S, T, a_domain, shares=None, rows=True):
+    dR, dS, dT = cu(R), cu(S), cu(T)
+    want = oracle.cyclic(R, S, T, oracle.GROUP_BY_A, a_domain=a_domain)
+    got = ctx.join3_cyclic(dR, dS, dT, "count", shares=shares)
+    assert int(got["total"].item()) == want["total"]
+    got = ctx.join3_cyclic(dR, dS, dT, "group_by_a", shares=shares, a_domain=a_domain)
+    assert int(got["total"].item()) == want["total"]
+    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+    if rows:
+        n = want["total"]
+        wr = oracle.cyclic(R, S, T, oracle.MATERIALIZE, capacity=n)
+        got = ctx.join3_cyclic(dR, dS, dT, "rows", shares=shares, capacity=n + 3)
+        assert int(got["n_rows"].item()) == n
+        assert np.array_equal(sorted_rows(got["rows"].cpu().numpy()), wr["rows"])
+
+
+def oriented(edges):
+    a = np.array([min(u, v) for u, v in edges], dtype=np.int32)
+    b = np.array([max(u, v) for u, v in edges], dtype=np.int32)
+    return datagen.triangle_relations(a, b)
+
+
+@pytest.mark.parametrize("n", [3, 10, 60])
+def test_complete_graph(ctx, n):
+    R, S, T = oriented(list(itertools.combinations(range(n), 2)))
+    got = ctx.join3_cyclic(cu(R), cu(S), cu(T), "count")
+    assert int(got["total"].item()) == math.comb(n, 3)
+    check_all_modes(ctx, R, S, T, n)
+
+
+@pytest.mark.parametrize("shares", [(1, 1, 1), (3, 5, 7), (16, 1, 1), (1, 16, 1), (1, 1, 16),
+                                    (8, 8, 8)])
+def test_share_invariance(ctx, shares):
+    a, b = datagen.chung_lu_undirected(n_vertices=1 << 12, mean_degree=12.0, seed=77)
+    R, S, T = datagen.triangle_relations(a, b)
+    check_all_modes(ctx, R, S, T, 1 << 12, shares=shares)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_bags(ctx, seed):
+    g = np.random.default_rng(200 + seed)
+    da, db, dc = (int(g.integers(1, 6)) for _ in range(3))
+    nR, nS, nT = (int(g.integers(0, 50)) for _ in range(3))
+    R = (g.integers(0, da, nR).astype(np.int32), g.integers(-1, db, nR).astype(np.int32))
+    S = (g.integers(-1, db, nS).astype(np.int32), g.integers(-1, dc, nS).astype(np.int32))
+    T = (g.integers(-1, dc, nT).astype(np.int32), g.integers(0, da, nT).astype(np.int32))
+    check_all_modes(ctx, R, S, T, max(da, 1))
+
+
+def test_extreme_keys_and_minus_one_pairs(ctx):
+    vals = np.array([-2**31, 2**31 - 1, -1, 0, 5], dtype=np.int32)
+    g = np.random.default_rng(9)
+    n = 400
+    R = (g.integers(0, 5, n).astype(np.int32), vals[g.integers(0, 5, n)])
+    S = (vals[g.integers(0, 5, n)], vals[g.integers(0, 5, n)])
+    T = (vals[g.integers(0, 5, n)], g.integers(0, 5, n).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 5, rows=False)
+    # T tuples equal to (-1, -1) as a (c, a) pair need a domain containing a = -1:
+    R2 = (np.full(7, -1, np.int32), np.array([3, 3, 4, -1, 3, 0, 0], np.int32))
+    S2 = (np.array([3, -1, 4, 3], np.int32), np.array([-1, -1, -1, 2], np.int32))
+    T2 = (np.array([-1, -1, 2], np.int32), np.array([-1, -1, -1], np.int32))
+    want = oracle.cyclic(R2, S2, T2)["total"]
+    assert want > 0
+    assert int(ctx.join3_cyclic(cu(R2), cu(S2), cu(T2), "count")["total"].item()) == want
+
+
+def test_empty(ctx):
+    E = (np.zeros(0, np.int32), np.zeros(0, np.int32))
+    R, S, T = oriented([(0, 1), (1, 2), (0, 2)])
+    for args in [(E, S, T), (R, E, T), (R, S, E)]:
+        check_all_modes(ctx, *args, a_domain=3)
+
+
+def test_big_tiles_split_into_items(ctx):
+    # one tile (shares 1,1,1) with R and T far above a chunk: many work items
+    g = np.random.default_rng(4)
+    n = 20000
+    R = (g.integers(0, 300, n).astype(np.int32), g.integers(0, 200, n).astype(np.int32))
+    S = (g.integers(0, 200, n).astype(np.int32), g.integers(0, 100, n).astype(np.int32))
+    T = (g.integers(0, 100, n).astype(np.int32), g.integers(0, 300, n).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 300, shares=(1, 1, 1), rows=False)
+    check_all_modes(ctx, R, S, T, 300, shares=(2, 2, 3), rows=False)
+
+
+def test_skewed_zipf(ctx):
+    g = np.random.default_rng(12)
+    q = datagen.random_query(g, "cyclic", size_lo=8000, size_hi=16000, dom_lo=100, dom_hi=1000,
+                             zipf=True, zipf_s=1.3)
+    check_all_modes(ctx, q.R, q.S, q.T, q.domains[0], rows=False)
+
+
+def test_domain_and_capacity_errors(ctx):
+    R, S, T = oriented([(0, 1), (1, 2), (0, 2), (2, 3), (1, 3)])
+    with pytest.raises(binding.MwjError) as ei:
+        ctx.join3_cyclic(cu(R), cu(S), cu(T), "group_by_a", a_domain=1)
+    assert ei.value.status == binding.MWJ_ERR_DOMAIN
+    with pytest.raises(binding.MwjError) as ei:
+        ctx.join3_cyclic(cu(R), cu(S), cu(T), "rows", capacity=1)
+    assert ei.value.status == binding.MWJ_ERR_CAPACITY
+
+
+def test_powerlaw_graph_medium(ctx):
+    a, b = datagen.chung_lu_undirected(n_vertices=1 << 16, mean_degree=32.0, seed=5)
+    R, S, T = datagen.triangle_relations(a, b)
+    check_all_modes(ctx, R, S, T, 1 << 16, rows=True)
+
+
+def test_triangle_workload_full_size_sampled(ctx):
+    """2^22-vertex power-law graph: GPU GROUP BY A, checked exactly on a sample
+    of A values (the oracle joined with R restricted to them), plus
+    sum(counts) == total == materialised row count."""
+    a, b = datagen.chung_lu_undirected()
+    R, S, T = datagen.triangle_relations(a, b)
+    dR, dS, dT = cu(R), cu(S), cu(T)
+    n_v = 1 << 22
+    got = ctx.join3_cyclic(dR, dS, dT, "group_by_a", a_domain=n_v)
+    total = int(got["total"].item())
+    counts = got["counts"].cpu().numpy()
+    assert int(counts.sum()) == total
+    g = np.random.default_rng(1)
+    hubs = np.argsort(-np.bincount(a))[:5].astype(np.int32)   # the busiest A values too
+    sample = np.unique(np.concatenate([g.choice(a, 300), hubs]))
+    keep = np.isin(R[0], sample)
+    Rs = (R[0][keep], R[1][keep])
+    want = oracle.cyclic(Rs, S, T, oracle.GROUP_BY_A, a_domain=n_v)
+    assert np.array_equal(counts[sample], want["counts"][sample])
+    assert int(ctx.join3_cyclic(dR, dS, dT, "count")["total"].item()) == total

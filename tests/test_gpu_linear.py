@@ -136,3 +136,16 @@ def test_aliased_self_join(ctx):
 def test_uniform_config_full_size(ctx):
     R, S, T = datagen.linear_uniform()
     check_all_modes(ctx, R, S, T, 1 << 20, rows=False)
+
+
+def test_friends_workload_full_size(ctx):
+    """F |x| F |x| F GROUP BY A on the 2^20-vertex power-law graph, the benchmark
+    workload, with the shares the library plans for it: every count exact."""
+    F = datagen.chung_lu_directed()
+    dF = cu(F)
+    want = oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=1 << 20)
+    got = ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=1 << 20)
+    assert int(got["total"].item()) == want["total"]
+    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+    got = ctx.join3_linear(dF, dF, dF, "count")
+    assert int(got["total"].item()) == want["total"]
