@@ -111,8 +111,11 @@ mwj_status mwj_create(mwj_ctx **ctx, const mwj_config *cfg);
 mwj_status mwj_destroy(mwj_ctx *ctx);
 
 /* Bytes of device workspace a call needs.  kind: MWJ_LINEAR / MWJ_CYCLIC for
- * mwj_join3_*, or 2 + kind for mwj_cascade_join (the cascade then uses any
- * extra bytes it is given as room for its intermediate relation). */
+ * mwj_join3_*, or 2 + kind for mwj_cascade_join.  For the cascade the size
+ * includes room for 2^24 rows of the intermediate relation I; the cascade
+ * uses every byte it is given beyond its fixed part as room for I, at 12
+ * bytes per row (linear), 20 (cyclic counts) or 24 (cyclic rows), and works
+ * through I in chunks of that many rows. */
 mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
                               const mwj_shares *shares, mwj_mode mode, size_t *bytes);
 

@@ -33,9 +33,12 @@ size_t part_scratch_bytes(int64_t n, uint32_t P, int num_sms);
 // Partition (x,y)[0,n) into `out` (uint2 pairs for PAY_PAIR, uint32 for
 // PAY_X/PAY_Y) grouped by bucket; bucket_off[0..P] receives the offsets.
 // Returns a cudaError_t of the launches.
+// With z != null the pairs (x,y) carry a third column z, written to outz in
+// the same order (PAY_PAIR only).
 cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n, const PartSpec &spec,
                      int payload, void *out, uint32_t *bucket_off, void *scratch,
-                     size_t scratch_bytes, int num_sms, cudaStream_t st);
+                     size_t scratch_bytes, int num_sms, cudaStream_t st,
+                     const int32_t *z = nullptr, int32_t *outz = nullptr);
 
 // ---- scans --------------------------------------------------------------
 size_t scan_scratch_bytes(size_t n);

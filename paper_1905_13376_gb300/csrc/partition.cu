@@ -261,6 +261,27 @@ __global__ void __launch_bounds__(PT) k_part_scatter_direct(
     }
 }
 
+// K3 with a third carried column z (pairs + z, direct scatter): the cascade's
+// second cyclic join partitions I(a,b,c) by (c,a) and carries b.
+__global__ void __launch_bounds__(PT) k_part_scatter_z(
+    const int32_t *__restrict__ x, const int32_t *__restrict__ y, const int32_t *__restrict__ z,
+    uint32_t n, PartSpec sp, uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
+    uint2 *__restrict__ out, int32_t *__restrict__ outz) {
+    extern __shared__ uint32_t cur[];
+    const uint32_t P = sp.P();
+    const uint32_t G = gridDim.x;
+    for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] = scanned[(size_t)b * G + blockIdx.x];
+    __syncthreads();
+    Chunk c = cta_chunk(n, tiles_per_cta);
+    for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
+        int32_t xv = __ldg(x + i), yv = __ldg(y + i);
+        uint32_t b = bucket_tuple(xv, yv, sp);
+        uint32_t p = atomicAdd(&cur[b], 1u);
+        out[p] = make_uint2((uint32_t)xv, (uint32_t)yv);
+        outz[p] = __ldg(z + i);
+    }
+}
+
 struct Geometry {
     uint32_t G, tiles_per_cta;
 };
@@ -316,7 +337,8 @@ size_t part_scratch_bytes(int64_t n, uint32_t P, int num_sms) {
 
 cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const PartSpec &sp,
                      int payload, void *out, uint32_t *bucket_off, void *scratch,
-                     size_t scratch_bytes, int num_sms, cudaStream_t st) {
+                     size_t scratch_bytes, int num_sms, cudaStream_t st, const int32_t *z,
+                     int32_t *outz) {
     const uint32_t P = sp.P();
     if (P == 0 || P > kMaxBuckets || n64 < 0 || n64 > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     if (scratch_bytes < part_scratch_bytes(n64, P, num_sms)) return cudaErrorInvalidValue;
@@ -363,6 +385,15 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     const bool need_y = sp.col1 == 1 || sp.col2 == 1 || payload == PAY_PAIR || payload == PAY_Y;
     if (!need_y) y = x;
     if (!need_x) x = y;
+    if (z) {
+        size_t smem = P * sizeof(uint32_t);
+        e = cudaFuncSetAttribute(k_part_scatter_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ProfScope ps_("part_scatter_z", st);
+        k_part_scatter_z<<<g.G, PT, smem, st>>>(x, y, z, n, sp, g.tiles_per_cta, counts, (uint2 *)out,
+                                                outz);
+        return cudaGetLastError();
+    }
     switch (payload) {
         case PAY_PAIR: return scatter_launch<PAY_PAIR>(x, y, n, sp, g, counts, out, st);
         case PAY_X: return scatter_launch<PAY_X>(x, y, n, sp, g, counts, out, st);

@@ -36,7 +36,7 @@ def check_all_modes(ctx, R, S, T, a_domain, shares=None, rows=True):
 
 
 def test_uniform_small(ctx):
-    R, S, T = datagen.linear_uniform(n=5000, ad=300, bd=64, cd=64, dd=300, seed=11)
+    R, S, T = datagen.linear_uniform(n=2000, ad=300, bd=64, cd=64, dd=300, seed=11)
     check_all_modes(ctx, R, S, T, 300)
 
 
