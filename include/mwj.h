@@ -145,6 +145,28 @@ mwj_status mwj_cascade_join(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_re
                             const mwj_out *out, void *workspace, size_t ws_bytes,
                             void *stream);
 
+/* The linear join (COUNT or COUNT GROUP BY A only) for callers that cannot
+ * allocate device memory -- for example code running under another
+ * runtime's allocator, or a plug-in whose host process owns every device
+ * allocation.  It needs no context and no workspace: its scratch is a
+ * fixed 24 MiB device array inside the library, present on every GPU that
+ * loads the library until the process exits.  There is no counterpart in
+ * the paper.
+ *
+ * Limits: at most 2^18 tuples per relation and shares with s[0]*s[1] <= 1024
+ * (NULL shares: the library picks them); larger inputs return
+ * MWJ_ERR_WORKSPACE (use mwj_join3_linear with a workspace instead).
+ * out->mode must be MWJ_COUNT or MWJ_COUNT_GROUP_BY_A.
+ * Runs on the current device and `stream`, then synchronises `stream` and
+ * returns any device-side error (e.g. MWJ_ERR_DOMAIN) directly.
+ * The first call on a device looks up the scratch array's device address;
+ * make it before any stream capture.  All calls share the one array: calls
+ * that overlap on the GPU (other streams, other host threads) race, so the
+ * caller must serialise them.  Scratch that must start at zero is cleared by
+ * every call. */
+mwj_status mwj_join3_linear_noalloc(mwj_rel R, mwj_rel S, mwj_rel T, const mwj_shares *shares,
+                                    const mwj_out *out, void *stream);
+
 /* Synchronise `stream`, return the first device-side error recorded since the
  * previous call (MWJ_OK if none) and clear it. */
 mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream);

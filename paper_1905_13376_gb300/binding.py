@@ -80,6 +80,9 @@ _SIGS = {
     "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
+    "mwj_join3_linear_noalloc": (ctypes.c_int, [mwj_rel, mwj_rel, mwj_rel,
+                                                ctypes.POINTER(mwj_shares),
+                                                ctypes.POINTER(mwj_out), _P]),
     "mwj_plan_shares": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel, ctypes.c_int,
                                        ctypes.POINTER(mwj_shares), _P]),
     "mwj_last_error": (ctypes.c_char_p, [_P]),
