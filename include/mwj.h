@@ -171,6 +171,34 @@ mwj_status mwj_join3_linear_noalloc(mwj_rel R, mwj_rel S, mwj_rel T, const mwj_s
  * previous call (MWJ_OK if none) and clear it. */
 mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream);
 
+/* ---- batches of independent joins (COUNT(*) per query) -------------------
+ * Thousands of small 3-way joins of uneven sizes, linear and cyclic mixed,
+ * run by one persistent join kernel after one persistent partitioning kernel
+ * (the paper's tiling applied per query; no counterpart for batching in the
+ * paper).  mwj_batch_create plans every query (shares.s[0] == 0: the
+ * library chooses the shares from the sizes) and fixes the relations'
+ * device pointers; mwj_batch_launch enqueues the whole batch with no host
+ * round trip, so launches after the first one on a given workspace can be
+ * captured into a CUDA graph and replayed (the first launch on a workspace
+ * uploads the plan's descriptors and must happen outside a capture).
+ * counts: device, n int64 elements, overwritten with each query's COUNT(*).
+ * Linear queries take at most 4096 H(B) buckets, cyclic ones x*y, y*z and
+ * z*x at most 4096 each. */
+typedef struct {
+    int32_t kind;          /* MWJ_LINEAR or MWJ_CYCLIC */
+    mwj_rel R, S, T;       /* device relations, as for mwj_join3_* */
+    mwj_shares shares;     /* s[0] == 0: chosen by the library */
+} mwj_query;
+
+typedef struct mwj_batch mwj_batch;
+
+mwj_status mwj_batch_create(mwj_ctx *ctx, const mwj_query *queries, int32_t n, mwj_batch **batch);
+mwj_status mwj_batch_workspace_size(mwj_batch *batch, size_t *bytes);
+mwj_status mwj_batch_shares(mwj_batch *batch, int32_t q, mwj_shares *shares);
+mwj_status mwj_batch_launch(mwj_batch *batch, int64_t *counts, void *workspace, size_t ws_bytes,
+                            void *stream);
+mwj_status mwj_batch_destroy(mwj_batch *batch);
+
 /* The shares the planner would choose for these relations (host result in
  * *shares).  kind = MWJ_LINEAR or MWJ_CYCLIC.  Synchronises `stream`. */
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,

@@ -50,6 +50,11 @@ class mwj_out(ctypes.Structure):
                 ("n_rows", ctypes.c_void_p)]
 
 
+class mwj_query(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("R", mwj_rel), ("S", mwj_rel), ("T", mwj_rel),
+                ("shares", mwj_shares)]
+
+
 class mwj_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_int32), ("load_pct", ctypes.c_int32),
@@ -93,6 +98,12 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "mwj_reset_phase_times": (ctypes.c_int, [_P]),
     "mwj_version": (ctypes.c_char_p, []),
+    "mwj_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(mwj_query), ctypes.c_int32,
+                                        ctypes.POINTER(_P)]),
+    "mwj_batch_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "mwj_batch_shares": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(mwj_shares)]),
+    "mwj_batch_launch": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P]),
+    "mwj_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -291,3 +302,56 @@ class Context:
             if mode == MWJ_MATERIALIZE:
                 res["rows"] = res["rows"][:int(res["n_rows"].item())]
         return res
+
+
+class Batch:
+    """A planned batch of independent joins (COUNT(*) per query) on one context.
+
+    queries: list of (kind, R, S, T[, shares]) with device int32 column pairs.
+    """
+
+    def __init__(self, ctx: "Context", queries):
+        import torch
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self._keep = [q[1:4] for q in queries]   # the relations must outlive the batch
+        arr = (mwj_query * max(1, len(queries)))()
+        for i, q in enumerate(queries):
+            kind, R, S, T = q[:4]
+            sh = q[4] if len(q) > 4 and q[4] is not None else (0, 0, 0)
+            arr[i].kind = kind
+            arr[i].R, arr[i].S, arr[i].T = _rel(R), _rel(S), _rel(T)
+            for k in range(3):
+                arr[i].shares.s[k] = int(sh[k])
+        h = _P()
+        ctx._check(self.lib.mwj_batch_create(ctx.h, arr, len(queries), ctypes.byref(h)))
+        self.h = h
+        self.n = len(queries)
+        n = ctypes.c_size_t()
+        ctx._check(self.lib.mwj_batch_workspace_size(self.h, ctypes.byref(n)))
+        self.ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=ctx.device)
+        self.counts = torch.zeros(max(self.n, 1), dtype=torch.int64, device=ctx.device)
+
+    def shares(self, q):
+        sh = mwj_shares()
+        self.ctx._check(self.lib.mwj_batch_shares(self.h, q, ctypes.byref(sh)))
+        return tuple(sh.s)
+
+    def launch(self, stream=None):
+        """Enqueue the batch; returns the device counts tensor (no sync)."""
+        st = self.lib.mwj_batch_launch(self.h, ctypes.c_void_p(self.counts.data_ptr()),
+                                       ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                       self.ctx._stream(stream))
+        self.ctx._check(st)
+        return self.counts[: self.n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mwj_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -162,11 +162,29 @@ def _log_uniform_int(g, lo: int, hi: int) -> int:
     return int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
 
 
+_HARMONIC = {}
+
+
+def _harmonic(s: float, size: int = 1 << 20) -> np.ndarray:
+    """Cumulative weights H[k] = sum_{i<=k} (i+1)^-s for k < size (cached per s)."""
+    key = round(float(s), 6)
+    h = _HARMONIC.get(key)
+    if h is None or len(h) < size:
+        h = np.cumsum(np.power(np.arange(1, size + 1, dtype=np.float64), -s))
+        _HARMONIC[key] = h
+    return h
+
+
 def _keys(g, n: int, domain: int, zipf: bool, s: float = 1.0) -> np.ndarray:
     if not zipf:
         return g.integers(0, domain, size=n, dtype=np.int64).astype(np.int32)
-    p = 1.0 / np.power(np.arange(1, domain + 1, dtype=np.float64), s)
-    k = _sample_by_weight(g, p, n)
+    # exact inverse CDF of P(k) proportional to (k+1)^-s on [0, domain)
+    H = _harmonic(s, max(domain, 1 << 20))[:domain]
+    # (searching sorted draws and shuffling the result gives the same i.i.d.
+    # sample faster)
+    k = np.searchsorted(H, np.sort(g.random(n)) * H[-1], side="right")
+    g.shuffle(k)
+    k = np.minimum(k, domain - 1).astype(np.int64)
     # bijection of [0, domain): k -> (k * mult + off) mod domain, gcd(mult, domain) = 1
     while True:
         mult = int(g.integers(1, max(2, domain)))
