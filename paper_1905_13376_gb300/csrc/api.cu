@@ -82,6 +82,7 @@ struct LinLayout {
     uint32_t *Tk; uint2 *Tp; uint32_t *offT;
     uint64_t *img; uint32_t *capT; uint32_t *startT; int32_t *dlist;
     uint32_t *ekey, *ecnt, *ecount, *meta;
+    unsigned int *hll;
     void *pscratch; size_t pscratch_bytes;
     unsigned long long *rowcount, *base; void *sscratch;
 };
@@ -92,22 +93,26 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
     L.offR = A.take<uint32_t>(p.I + 1);
     L.Sp = A.take<uint2>(S.n + 2);
     L.offS = A.take<uint32_t>((size_t)p.I * p.J + 1);
-    if (p.rows) {
-        L.Tk = nullptr;
-        L.Tp = A.take<uint2>(T.n + 2);
-    } else {
-        L.Tk = A.take<uint32_t>(T.n + 4);
-        L.Tp = nullptr;
-    }
-    L.offT = A.take<uint32_t>(p.JT + 1);
     if (p.single) {
+        // T stays unpartitioned: one table sized from a HyperLogLog estimate
+        L.Tk = nullptr;
+        L.Tp = nullptr;
+        L.offT = nullptr;
         L.img = A.take<uint64_t>(single_table_slots(T.n));
         L.capT = nullptr;
-        L.ekey = A.take<uint32_t>(T.n + 4);
-        L.ecnt = A.take<uint32_t>(T.n + 4);
-        L.ecount = A.take<uint32_t>(p.JT + 1);
+        L.ekey = L.ecnt = L.ecount = nullptr;
         L.meta = A.take<uint32_t>(4);
+        L.hll = A.take<unsigned int>(hll_registers());
     } else {
+        if (p.rows) {
+            L.Tk = nullptr;
+            L.Tp = A.take<uint2>(T.n + 2);
+        } else {
+            L.Tk = A.take<uint32_t>(T.n + 4);
+            L.Tp = nullptr;
+        }
+        L.offT = A.take<uint32_t>(p.JT + 1);
+        L.hll = nullptr;
         L.img = A.take<uint64_t>(2 * (size_t)T.n + 4);
         L.capT = A.take<uint32_t>(p.JT + 1);
         L.ekey = L.ecnt = L.ecount = L.meta = nullptr;
@@ -126,7 +131,7 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
     }
     size_t ps = part_scratch_bytes(R.n, p.I, num_sms);
     size_t ps2 = part_scratch_bytes(S.n, p.I * p.J, num_sms);
-    size_t ps3 = part_scratch_bytes(T.n, p.JT, num_sms);
+    size_t ps3 = p.single ? 0 : part_scratch_bytes(T.n, p.JT, num_sms);
     if (ps2 > ps) ps = ps2;
     if (ps3 > ps) ps = ps3;
     L.pscratch = A.take<char>(ps);
@@ -327,11 +332,14 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
         (e = cudaMemsetAsync(out->group_counts, 0, sizeof(int64_t) * (size_t)out->a_domain, st)) !=
             cudaSuccess)
         return cuda_fail(ctx, e, "memset group_counts");
-    // Algorithm 1, steps 1-3: T by g(C), S by (H(B), g(C)), R by H(B)
-    PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
-    e = part_run(T.x, T.y, T.n, pt, p.rows ? PAY_PAIR : PAY_X, p.rows ? (void *)L.Tp : (void *)L.Tk,
-                 L.offT, L.pscratch, L.pscratch_bytes, ctx->dev.num_sms, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");
+    // Algorithm 1, steps 1-3: T by g(C), S by (H(B), g(C)), R by H(B).  With
+    // one g(C) bucket T is not partitioned: its C table is built directly.
+    if (!p.single) {
+        PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
+        e = part_run(T.x, T.y, T.n, pt, p.rows ? PAY_PAIR : PAY_X, p.rows ? (void *)L.Tp : (void *)L.Tk,
+                     L.offT, L.pscratch, L.pscratch_bytes, ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");
+    }
     PartSpec ps{0, sd.B, p.I, p.J > 1 ? 1 : -1, sd.C, p.J};
     e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
@@ -346,8 +354,8 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
     // T's tables
     if (p.single)
-        e = single_table_build(L.Tk, L.offT, p.JT, sd.slot2, L.ekey, L.ecnt, L.ecount, L.meta, L.img,
-                               ctx->status, ctx->dev.num_sms, st);
+        e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
+                                ctx->status, ctx->dev.num_sms, st);
     else
         e = tables_build(L.Tk, L.Tp, L.offT, p.JT, sd.slot2, L.img, L.capT, L.startT, L.dlist,
                          ctx->status, ctx->dev.num_sms, st);

@@ -363,3 +363,151 @@ cudaError_t tables_build(const uint32_t *keys, const uint2 *pairs, const uint32_
 }
 
 }  // namespace mwj
+
+// ---------------------------------------------------------------------------
+// single table without partitioning T: size it from a HyperLogLog estimate
+// of T's distinct C values, then insert T's C column directly
+// ---------------------------------------------------------------------------
+namespace mwj {
+namespace {
+
+constexpr int HLL_BITS = 12;
+constexpr uint32_t HLL_M = 1u << HLL_BITS;
+
+// HyperLogLog registers (Flajolet, Fusy, Gandouet, Meunier 2007): register
+// h >> (32 - HLL_BITS) keeps the largest rank (position of the first 1 bit)
+// of the remaining bits.  mix32 is a bijection of 32-bit keys, so distinct
+// keys have distinct hashes.
+__global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, uint32_t n,
+                                            uint32_t seed, unsigned int *__restrict__ regs) {
+    __shared__ unsigned int r[HLL_M];
+    for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) r[j] = 0;
+    __syncthreads();
+    const bool vec = ((uintptr_t)keys & 15) == 0;
+    const uint32_t stride = gridDim.x * BT * 4;
+    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * 4; i < n; i += stride) {
+        int32_t v[4];
+        if (vec && i + 3 < n) {
+            int4 q = __ldg((const int4 *)(keys + i));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i + k >= n) break;
+            const uint32_t h = mix32((uint32_t)v[k] ^ seed);
+            const uint32_t w = h << HLL_BITS;
+            const uint32_t rank = (w == 0) ? (33u - HLL_BITS) : (uint32_t)__clz(w) + 1u;
+            atomicMax(&r[h >> (32 - HLL_BITS)], rank);
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < HLL_M; j += BT)
+        if (r[j]) atomicMax(&regs[j], r[j]);
+}
+
+// estimate -> table of 2^k >= 4 x estimate slots (at most `reserve`)
+__global__ void k_hll_size(const unsigned int *__restrict__ regs, uint64_t reserve,
+                           uint32_t *__restrict__ meta) {
+    __shared__ double part[32];
+    __shared__ unsigned int zeros[32];
+    double s = 0.0;
+    unsigned int z = 0;
+    for (uint32_t j = threadIdx.x; j < HLL_M; j += blockDim.x) {
+        s += ldexp(1.0, -(int)regs[j]);
+        z += (regs[j] == 0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[threadIdx.x >> 5] = s;
+        zeros[threadIdx.x >> 5] = z;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        unsigned int Z = 0;
+        for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+            S += part[w];
+            Z += zeros[w];
+        }
+        const double m = (double)HLL_M;
+        double E = (0.7213 / (1.0 + 1.079 / m)) * m * m / S;
+        if (E <= 2.5 * m && Z > 0) E = m * log(m / (double)Z);   // small-range correction
+        uint64_t cap = 16;
+        while ((double)cap < 4.0 * E && cap < reserve) cap <<= 1;
+        if (cap > reserve) cap = reserve;
+        meta[0] = (uint32_t)(cap - 1);
+        meta[1] = (uint32_t)E;
+    }
+}
+
+// insert T's C column; each thread merges runs of equal keys among 8
+// consecutive tuples before touching the table
+__global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict__ keys, uint32_t n,
+                                                       uint32_t seed, unsigned long long *__restrict__ tbl,
+                                                       const uint32_t *__restrict__ meta, DevStatus *st) {
+    const uint32_t mask = meta[0];
+    const bool vec = ((uintptr_t)keys & 15) == 0;
+    const uint32_t stride = gridDim.x * BT * 8;
+    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * 8; i < n; i += stride) {
+        int32_t v[8];
+        if (vec && i + 7 < n) {
+            int4 a = __ldg((const int4 *)(keys + i));
+            int4 b = __ldg((const int4 *)(keys + i + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
+        }
+        const uint32_t m = min(8u, n - i);
+        uint32_t cur = (uint32_t)v[0], run = 1;
+        for (uint32_t k = 1; k < m; ++k) {
+            if ((uint32_t)v[k] == cur) {
+                ++run;
+            } else {
+                single_insert(tbl, mask, cur, seed, run, st);
+                cur = (uint32_t)v[k];
+                run = 1;
+            }
+        }
+        single_insert(tbl, mask, cur, seed, run, st);
+    }
+}
+
+}  // namespace
+
+cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
+                                uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
+                                DevStatus *status, int num_sms, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    const uint32_t nn = (uint32_t)n;
+    if (nn > 0) {
+        ProfScope ps_("t_hll", st);
+        k_hll<<<num_sms * 2, BT, 0, st>>>(keys, nn, seed, hll_regs);
+    }
+    {
+        ProfScope ps_("t_size", st);
+        k_hll_size<<<1, 1024, 0, st>>>(hll_regs, reserve_slots, meta);
+    }
+    {
+        ProfScope ps_("t_clear", st);
+        k_tclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)tbl, meta);
+    }
+    if (nn > 0) {
+        ProfScope ps_("t_insert", st);
+        k_tinsert_direct<<<num_sms * 4, BT, 0, st>>>(keys, nn, seed, (unsigned long long *)tbl, meta,
+                                                      status);
+    }
+    return cudaGetLastError();
+}
+
+uint32_t hll_registers() { return HLL_M; }
+
+}  // namespace mwj

@@ -61,4 +61,12 @@ cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32
                                uint32_t *ekey, uint32_t *ecnt, uint32_t *ecount, uint32_t *meta,
                                uint64_t *tbl, DevStatus *status, int num_sms, cudaStream_t st);
 
+// One table without partitioning T: a HyperLogLog pass over the keys sizes
+// the table (2^k >= 4 x the estimate, at most reserve_slots), then the keys
+// are inserted directly.  hll_regs: hll_registers() u32; meta: 2 u32.
+cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
+                                uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
+                                DevStatus *status, int num_sms, cudaStream_t st);
+uint32_t hll_registers();
+
 }  // namespace mwj
