@@ -225,6 +225,49 @@ int mwj_get_phase_times(mwj_ctx *ctx, const char **names, double *ms, long long 
                         int max);
 mwj_status mwj_reset_phase_times(mwj_ctx *ctx);
 
+/* ---- planning: features, cost model, learned planner ----------------------
+ * A plan only chooses between the 3-way join and the cascade and scales the
+ * shares; it never changes a result.
+ *
+ * mwj_features writes 24 floats (host) describing a join instance: log2 of
+ * the three sizes, log2 of HyperLogLog distinct counts of R.x, R.y, S.y, T.y,
+ * the cyclic flag, log2 of a sampled estimate of |R join S| (the exact R
+ * degrees of evenly spaced S tuples, scaled), and sampled key-frequency
+ * fractions (once / 2-7 / 8+ times in the sample) of R.y, S.x, S.y, T.x and
+ * T.y (cyclic only).  workspace: device, >= mwj_features_workspace_size().
+ * Synchronises `stream`.
+ *
+ * mwj_cost_model: from the features, out3[0] = log2 predicted seconds of
+ * the cascade, out3[1] = of the 3-way join, out3[2] = log2 share scale (0).
+ * It restates the tuple counts of Sections 4.2, 5.2 and 6.3 as HBM bytes and
+ * random lookups (the paper's Appendix A model, a phase costs its slowest
+ * resource), with hbm_gbs the HBM bandwidth in GB/s.
+ *
+ * mwj_mlp_*: the planner's network, 24 -> 128 -> 128 -> 3 with ReLU, BF16
+ * weights and activations, FP32 accumulation and FP32 Adam master weights
+ * (mwj_mlp_num_params() floats in the layout W1[24][128], b1[128],
+ * W2[128][128], b2[128], W3[128][3], b3[3]).  X: device B x 24 floats
+ * (rounded to BF16 on entry), Y: device B x 3.  backward writes the FP32
+ * gradient of sum M (Y - T)^2 * inv_count into grads (device,
+ * mwj_mlp_num_params()) and the loss into *loss (device); adam applies one
+ * Adam step (beta 0.9 / 0.999, eps 1e-8; step >= 1 is the bias-correction
+ * count). */
+size_t mwj_features_workspace_size(void);
+mwj_status mwj_features(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, float *features,
+                        void *workspace, size_t ws_bytes, void *stream);
+mwj_status mwj_cost_model(const float *features, double hbm_gbs, double *out3);
+
+typedef struct mwj_mlp mwj_mlp;
+size_t mwj_mlp_num_params(void);
+mwj_status mwj_mlp_create(mwj_ctx *ctx, mwj_mlp **mlp);
+mwj_status mwj_mlp_destroy(mwj_mlp *mlp);
+mwj_status mwj_mlp_set_params(mwj_mlp *mlp, const float *host_params);
+mwj_status mwj_mlp_get_params(mwj_mlp *mlp, float *host_params);
+mwj_status mwj_mlp_forward(mwj_mlp *mlp, const float *X, int32_t B, float *Y, void *stream);
+mwj_status mwj_mlp_backward(mwj_mlp *mlp, const float *X, const float *T, const float *M, int32_t B,
+                            float inv_count, float *grads, float *loss, void *stream);
+mwj_status mwj_mlp_adam(mwj_mlp *mlp, const float *grads, float lr, int32_t step, void *stream);
+
 /* Library version string, e.g. "mwj 0.1 sm_103a". */
 const char *mwj_version(void);
 

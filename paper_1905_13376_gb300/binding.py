@@ -98,6 +98,20 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "mwj_reset_phase_times": (ctypes.c_int, [_P]),
     "mwj_version": (ctypes.c_char_p, []),
+    "mwj_features_workspace_size": (ctypes.c_size_t, []),
+    "mwj_features": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
+                                    ctypes.POINTER(ctypes.c_float), _P, ctypes.c_size_t, _P]),
+    "mwj_cost_model": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "mwj_mlp_num_params": (ctypes.c_size_t, []),
+    "mwj_mlp_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "mwj_mlp_destroy": (ctypes.c_int, [_P]),
+    "mwj_mlp_set_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "mwj_mlp_get_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "mwj_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "mwj_mlp_backward": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, _P, _P,
+                                        _P]),
+    "mwj_mlp_adam": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_int32, _P]),
     "mwj_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(mwj_query), ctypes.c_int32,
                                         ctypes.POINTER(_P)]),
     "mwj_batch_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -348,6 +362,83 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.mwj_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cost_model(features, hbm_gbs: float = 6792.1):
+    """The library's cost model on a host feature vector (24 floats)."""
+    lib = load()
+    f = (ctypes.c_float * 24)(*[float(v) for v in features])
+    out = (ctypes.c_double * 3)()
+    st = lib.mwj_cost_model(f, float(hbm_gbs), out)
+    if st != MWJ_OK:
+        raise MwjError(st, "mwj_cost_model")
+    return list(out)
+
+
+class MLP:
+    """The planner network on the GPU (BF16 weights/activations, FP32 accumulate)."""
+
+    def __init__(self, ctx: "Context", params=None):
+        import numpy as np
+        import torch
+        self.ctx, self.lib = ctx, ctx.lib
+        h = _P()
+        ctx._check(self.lib.mwj_mlp_create(ctx.h, ctypes.byref(h)))
+        self.h = h
+        self.n = int(self.lib.mwj_mlp_num_params())
+        self.grads = torch.zeros(self.n, dtype=torch.float32, device=ctx.device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=ctx.device)
+        self.step = 0
+        if params is not None:
+            self.set_params(np.asarray(params, dtype=np.float32))
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n
+        self.ctx._check(self.lib.mwj_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        self.step = 0
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.n, dtype=np.float32)
+        self.ctx._check(self.lib.mwj_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous().float()
+        Y = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        self.ctx._check(self.lib.mwj_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                                 ctypes.c_void_p(Y.data_ptr()),
+                                                 self.ctx._stream(None)))
+        return Y
+
+    def backward(self, X, T, M):
+        X, T, M = (t.contiguous().float() for t in (X, T, M))
+        cnt = float(max(1.0, float(M.sum().item())))
+        self.ctx._check(self.lib.mwj_mlp_backward(
+            self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+            ctypes.c_void_p(M.data_ptr()), X.shape[0], 1.0 / cnt,
+            ctypes.c_void_p(self.grads.data_ptr()), ctypes.c_void_p(self.loss.data_ptr()),
+            self.ctx._stream(None)))
+        return self.grads, self.loss
+
+    def adam(self, lr):
+        self.step += 1
+        self.ctx._check(self.lib.mwj_mlp_adam(self.h, ctypes.c_void_p(self.grads.data_ptr()),
+                                              float(lr), self.step, self.ctx._stream(None)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mwj_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

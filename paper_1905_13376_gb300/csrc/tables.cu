@@ -510,4 +510,15 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
 
 uint32_t hll_registers() { return HLL_M; }
 
+cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *regs, int num_sms,
+                     cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    if (n > 0) {
+        ProfScope ps_("sketch_hll", st);
+        k_hll<<<num_sms * 2, BT, 0, st>>>(keys, (uint32_t)n, seed, regs);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace mwj

@@ -68,5 +68,8 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
                                 DevStatus *status, int num_sms, cudaStream_t st);
 uint32_t hll_registers();
+// HyperLogLog registers of keys[0, n) into regs (hll_registers() u32, cleared first)
+cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *regs, int num_sms,
+                     cudaStream_t st);
 
 }  // namespace mwj
