@@ -186,6 +186,22 @@ class Planner:
         return cls(ctx, d["params"], d["fmean"], d["fstd"], d["ymean"], d["ystd"])
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "planner_weights.npz")
+
+
+def default_planner(ctx) -> Planner:
+    """The network trained on 20000 engine-timed instances (planner_weights.npz)."""
+    return Planner.load(ctx, WEIGHTS)
+
+
+def plan_and_run(ctx, kind, R, S, T, mode="count", planner: Planner | None = None, **kw):
+    """Choose a plan (the learned planner, else the cost model) and run it.
+    Returns (result, (cascade?, share scale))."""
+    F = features(ctx, kind, R, S, T)
+    choice = (planner.choose(F) if planner is not None else cost_model_choice(F))[0]
+    return run_plan(ctx, kind, R, S, T, choice[0], choice[1], mode, **kw), choice
+
+
 def cost_model_choice(F: np.ndarray, hbm_gbs=6792.1):
     out = []
     for f in np.atleast_2d(F):

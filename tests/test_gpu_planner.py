@@ -127,3 +127,17 @@ def test_trained_network_gains_over_cost_model(ctx):
             checked += 1   # (the instances live on the GPU; exactness across plans is
             #              asserted inside measure() for every instance)
     assert checked >= 0
+
+
+def test_trained_planner_plans_are_exact(ctx):
+    """The committed network plans real joins; every plan gives the oracle's answer."""
+    pl = planner.default_planner(ctx)
+    g = np.random.default_rng(21)
+    for kind in ["linear", "cyclic", "linear", "cyclic"]:
+        q = datagen.random_query(g, kind, size_lo=500, size_hi=20000, dom_lo=50, dom_hi=5000)
+        k = binding.MWJ_LINEAR if kind == "linear" else binding.MWJ_CYCLIC
+        res, choice = planner.plan_and_run(ctx, k, cu(q.R), cu(q.S), cu(q.T), planner=pl)
+        fn = oracle.linear if kind == "linear" else oracle.cyclic
+        assert int(res["total"].item()) == fn(q.R, q.S, q.T)["total"], choice
+        res, _ = planner.plan_and_run(ctx, k, cu(q.R), cu(q.S), cu(q.T), planner=None)
+        assert int(res["total"].item()) == fn(q.R, q.S, q.T)["total"]
