@@ -343,7 +343,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--vertices", type=int, default=1 << 20)
-    ap.add_argument("--shares", type=int, nargs=2, default=None)
+    ap.add_argument("--shares", type=int, nargs="+", default=None,
+                    help="I J [log2 table slots]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
     args = ap.parse_args()

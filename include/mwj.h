@@ -74,7 +74,10 @@ typedef struct {
  * 5 and the analyses 4.2, 5.2).
  *   linear: s[0] = number of H(B) buckets of R and S; s[1] = number of g(C)
  *           buckets of S and T (1 = T's tile stays whole in L2, see
- *           mwj_join3_linear); s[2] ignored.
+ *           mwj_join3_linear); s[2] = log2 of the slots of the on-chip R
+ *           bucket table, 9..14 (0 or 1: the library default, 12); a bucket
+ *           with more distinct B values than half the slots is processed in
+ *           chunks.
  *   cyclic: s = {H(A), G(B), F(C)} bucket counts; tile (i,j,k) joins
  *           R_ij, S_jk and T_ki.
  * Every used entry must be >= 1.  A NULL share pointer asks the library's

@@ -102,7 +102,7 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
         L.capT = nullptr;
         L.ekey = L.ecnt = L.ecount = nullptr;
         L.meta = A.take<uint32_t>(4);
-        L.hll = A.take<unsigned int>(hll_registers());
+        L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
     } else {
         if (p.rows) {
             L.Tk = nullptr;
@@ -148,8 +148,8 @@ mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S,
     (void)S;
     (void)T;
     // R bucket tables of 2^12 slots hold up to ~2K distinct B values; aim for
-    // ~16K tuples of R per bucket and at least four buckets per SM.
-    uint64_t want = (uint64_t)(R.n + 16383) / 16384;
+    // ~32K tuples of R per bucket and at least four buckets per SM.
+    uint64_t want = (uint64_t)(R.n + 32767) / 32768;
     uint64_t minb = (uint64_t)ctx->dev.num_sms * 4;
     if (want < minb) want = minb;
     uint32_t I = pow2_at_least(want);
@@ -162,6 +162,8 @@ mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S,
 
 mwj_status lin_check_shares(mwj_ctx *ctx, const mwj_shares *sh, uint32_t *I, uint32_t *J) {
     if (sh->s[0] < 1 || sh->s[1] < 1) return fail(ctx, MWJ_ERR_INVALID_ARG, "shares must be >= 1");
+    if (sh->s[2] > 1 && (sh->s[2] < 9 || sh->s[2] > 14))
+        return fail(ctx, MWJ_ERR_INVALID_ARG, "linear shares: s[2] (log2 table slots) must be 9..14");
     uint64_t P = (uint64_t)sh->s[0] * (uint64_t)sh->s[1];
     if ((uint64_t)sh->s[0] > kMaxBuckets || P > kMaxBuckets)
         return fail(ctx, MWJ_ERR_INVALID_ARG, "linear shares: I*J must be <= %u", kMaxBuckets);
@@ -367,13 +369,17 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
         g.t = TImg{L.img, nullptr, nullptr, nullptr, nullptr, L.meta, 0u, sd.C, sd.slot2};
     else
         g.t = TImg{L.img, L.offT, L.capT, L.startT, L.dlist, nullptr, p.JT, sd.C, sd.slot2};
-    g.cap_log2 = ctx->cap_log2;
+    // on-chip R table: 2^s[2] slots when given, else the context's default;
+    // row output keeps it at most 2^13 (it also holds the a-lists)
+    g.cap_log2 = (sh.s[2] >= 9) ? (uint32_t)sh.s[2] : ctx->cap_log2;
+    if (p.rows && g.cap_log2 > 13) g.cap_log2 = 13;
     g.seed_slot = sd.slot;
     g.a_domain = out->a_domain;
     g.cnt = (unsigned long long *)out->group_counts;
     g.total = (unsigned long long *)out->total;
     g.rowcount = L.rowcount;
     g.st = ctx->status;
+    g.spin_limit = (uint32_t)(ctx->spin_limit < (1ll << 24) ? ctx->spin_limit : (1ll << 24));
     int mode = out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0;
     if ((e = lin_agg_launch(g, mode, st)) != cudaSuccess) return cuda_fail(ctx, e, "linear probe");
     if (p.rows) {

@@ -26,6 +26,7 @@ namespace {
 
 constexpr int LT = 512;          // threads per CTA
 constexpr int ROUND = LT * 4;    // R tuples inserted per build round
+constexpr uint32_t RCH = 2048;   // R tuples per bulk-copy buffer of the tile build (two buffers)
 
 // Clear the table; values are cleared by the caller.
 __device__ __forceinline__ void tbl_clear(uint32_t *keys, uint32_t cap) {
@@ -74,43 +75,90 @@ __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, ui
     return cend < r1 ? cend : r1;
 }
 
-// One optimistic pass: insert every R tuple of [pos, r1) with probe sequences
-// of at most 32 slots.  Succeeds when no insert failed and the table ended at
-// most 3/4 full; otherwise the caller clears the table and builds in rounds.
-// Ends with a barrier.
+// Bulk-copy pipeline of two shared-memory buffers, each with a "full"
+// barrier: thread 0 refills a buffer after a CTA barrier has shown every
+// thread done with it.  Used to stage an R bucket tile into shared memory.
+struct Ring {
+    uint2 *buf;                     // 2 x RCH tuples
+    unsigned long long *full;       // 2 barriers
+    uint32_t uses[2];               // completed fills of each buffer (same in every thread)
+};
+
+// One optimistic pass over R tuples [pos, r1), staged through the ring by
+// bulk copies (16-byte aligned superset of the range, rows outside it are
+// skipped): insert every tuple with probe sequences of at most 32 slots.
+// Succeeds when no insert failed and the table ended at most 3/4 full;
+// otherwise the caller clears the table and builds in bounded rounds.
+// Returns -1 when a copy did not land within the wait limit.  Ends with a
+// barrier.
 template <typename F>
-__device__ __forceinline__ bool build_all(const uint2 *__restrict__ Rp, uint32_t pos, uint32_t r1,
-                                          uint32_t *keys, uint32_t cap, uint32_t seed,
-                                          uint32_t *nd, uint32_t *bad, F &&on_insert) {
+__device__ __forceinline__ int build_all(const uint2 *__restrict__ Rp, uint32_t pos, uint32_t r1,
+                                         uint32_t *keys, uint32_t cap, uint32_t seed, uint32_t *nd,
+                                         uint32_t *bad, Ring &ring, uint32_t spin_limit,
+                                         F &&on_insert) {
     const uint32_t mask = cap - 1;
+    const uint32_t a0 = pos & ~1u;
+    const uint32_t total = ((r1 - a0) + 1u) & ~1u;
+    const uint32_t nch = (total + RCH - 1) / RCH;
+    auto issue = [&](uint32_t c) {
+        const uint32_t b = c & 1u;
+        const uint32_t len = min(RCH, total - c * RCH);
+        fence_proxy_async();
+        mbar_expect_tx(&ring.full[b], len * 8u);
+        bulk_copy_g2s(ring.buf + b * RCH, Rp + a0 + c * RCH, len * 8u, &ring.full[b]);
+    };
+    if (threadIdx.x == 0) {
+        if (nch > 0) issue(0);
+        if (nch > 1) issue(1);
+    }
     uint32_t fresh_n = 0;
-    bool failed = false;
-    for (uint32_t idx = pos + threadIdx.x; idx < r1; idx += LT) {
-        uint2 t = __ldg(Rp + idx);
-        int slot;
-        bool fresh = false;
-        if (t.y == kEmptyKey) {
-            slot = tbl_insert(keys, mask, t.y, seed, &fresh);
-        } else {
-            slot = -1;
-            uint32_t s = mix32(t.y ^ seed) & mask;
-            for (int it = 0; it < 32; ++it) {
-                uint32_t q = keys[s];
-                if (q == t.y) { slot = (int)s; break; }
-                if (q == kEmptyKey) {
-                    uint32_t old = atomicCAS(&keys[s], kEmptyKey, t.y);
-                    if (old == kEmptyKey) { slot = (int)s; fresh = true; break; }
-                    if (old == t.y) { slot = (int)s; break; }
+    bool failed = false, late = false;
+    for (uint32_t c = 0; c < nch; ++c) {
+        const uint32_t b = c & 1u;
+        late |= !mbar_wait_bounded(&ring.full[b], ring.uses[b] & 1u, spin_limit);
+        ++ring.uses[b];
+        if (__syncthreads_or(late)) break;
+        const uint32_t len = min(RCH, total - c * RCH);
+        const uint32_t base = a0 + c * RCH;
+        const uint2 *src = ring.buf + b * RCH;
+        for (uint32_t j = threadIdx.x; j < len && !failed; j += LT) {
+            const uint32_t gi = base + j;
+            if (gi < pos || gi >= r1) continue;
+            const uint2 t = src[j];
+            int slot;
+            bool fresh = false;
+            if (t.y == kEmptyKey) {
+                slot = tbl_insert(keys, mask, t.y, seed, &fresh);
+            } else {
+                slot = -1;
+                uint32_t s = mix32(t.y ^ seed) & mask;
+                for (int it = 0; it < 32; ++it) {
+                    uint32_t q = keys[s];
+                    if (q == t.y) { slot = (int)s; break; }
+                    if (q == kEmptyKey) {
+                        uint32_t old = atomicCAS(&keys[s], kEmptyKey, t.y);
+                        if (old == kEmptyKey) { slot = (int)s; fresh = true; break; }
+                        if (old == t.y) { slot = (int)s; break; }
+                    }
+                    s = (s + 1) & mask;
                 }
-                s = (s + 1) & mask;
             }
+            if (slot < 0) {
+                failed = true;
+                break;
+            }
+            fresh_n += fresh;
+            on_insert(slot, t);
         }
-        if (slot < 0) {
-            failed = true;
-            break;
-        }
-        fresh_n += fresh;
-        on_insert(slot, t);
+        __syncthreads();   // every thread is done with buffer b
+        if (threadIdx.x == 0 && c + 2 < nch) issue(c + 2);
+    }
+    if (late) {
+        // wait (bounded) for the fills still in flight before giving up
+        if (threadIdx.x == 0)
+            for (uint32_t b = 0; b < 2; ++b) mbar_wait_bounded(&ring.full[b], ring.uses[b] & 1u, spin_limit);
+        __syncthreads();
+        return -1;
     }
     fresh_n = warp_sum(fresh_n);
     unsigned anyfail = __ballot_sync(0xffffffffu, failed);
@@ -119,7 +167,7 @@ __device__ __forceinline__ bool build_all(const uint2 *__restrict__ Rp, uint32_t
         if (anyfail) atomicOr(bad, 1u);
     }
     __syncthreads();
-    return !(*bad) && *nd <= cap - cap / 4;
+    return (!(*bad) && *nd <= cap - cap / 4) ? 1 : 0;
 }
 
 constexpr int NB = 4;   // tuples per thread per batch
@@ -215,6 +263,14 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
     uint32_t *whi = (uint32_t *)(smem + 2 * arr);      // MODE 1
     __shared__ uint32_t nd, bad;
     __shared__ unsigned long long red[32];
+    __shared__ __align__(8) unsigned long long fullb[2];
+    Ring ring{(uint2 *)(smem + (MODE == 0 ? 2 : 3) * arr), fullb, {0u, 0u}};
+    if (threadIdx.x == 0) {
+        mbar_init(&fullb[0], 1);
+        mbar_init(&fullb[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
 
     const uint32_t i = blockIdx.x;
     const uint32_t r0 = g.offR[i], r1 = g.offR[i + 1];
@@ -244,7 +300,14 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
             };
             uint32_t cend;
             __syncthreads();
-            if (pos == r0 && build_all(g.Rp, pos, r1, keys, cap, g.seed_slot, &nd, &bad, on_insert)) {
+            int fast = (pos == r0) ? build_all(g.Rp, pos, r1, keys, cap, g.seed_slot, &nd, &bad, ring,
+                                               g.spin_limit, on_insert)
+                                   : 0;
+            if (fast < 0) {   // a bulk copy did not arrive in time
+                if (threadIdx.x == 0) set_status(g.st, MWJ_ERR_TIMEOUT, (long long)blockIdx.x);
+                return;
+            }
+            if (fast) {
                 cend = r1;
             } else {
                 if (pos == r0) {   // the optimistic pass overflowed: start over in rounds
@@ -440,7 +503,7 @@ __global__ void k_rows_check(const unsigned long long *base, uint32_t I, long lo
 
 size_t lin_agg_smem(uint32_t cap_log2, int mode) {
     uint32_t cap = 1u << cap_log2;
-    return align256((cap + 1) * 4) * (mode == 1 ? 3 : 2);
+    return align256((cap + 1) * 4) * (mode == 1 ? 3 : 2) + 2 * RCH * sizeof(uint2);
 }
 
 size_t lin_rows_smem(uint32_t cap_log2, uint32_t max_tuples) {

@@ -19,6 +19,7 @@ struct LinArgs {
     unsigned long long *total;
     unsigned long long *rowcount;   // per R bucket (row output, pass 1), or null
     DevStatus *st;
+    uint32_t spin_limit;        // polls of a bounded barrier wait before MWJ_ERR_TIMEOUT
 };
 
 size_t lin_agg_smem(uint32_t cap_log2, int mode);

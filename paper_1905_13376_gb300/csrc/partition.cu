@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
     uint32_t *cnt = cur + P;                             // P: tile counts
     uint32_t *off = cnt + P;                             // P: tile offsets
     T *stage = (T *)(smem + align256(3 * P * sizeof(uint32_t)));   // TILE
-    uint16_t *sbk = (uint16_t *)(stage + TILE);          // TILE bucket ids
+    uint32_t *gpos = (uint32_t *)(stage + TILE);         // TILE: output position of each staged tuple
     __shared__ uint32_t scan_scratch[33];
 
     const uint32_t G = gridDim.x;
@@ -226,14 +226,12 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
             if (bk[j] != 0xFFFFFFFFu) {
                 uint32_t p = off[bk[j]] + rk[j];
                 stage[p] = pv[j];
-                sbk[p] = (uint16_t)bk[j];
+                gpos[p] = cur[bk[j]] + rk[j];
             }
         }
         __syncthreads();
-        for (uint32_t e = threadIdx.x; e < tn; e += PT) {
-            uint32_t b = sbk[e];
-            out[cur[b] + (e - off[b])] = stage[e];
-        }
+        // consecutive threads write consecutive positions of each bucket's run
+        for (uint32_t e = threadIdx.x; e < tn; e += PT) out[gpos[e]] = stage[e];
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] += cnt[b];
         __syncthreads();
@@ -308,7 +306,7 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
     using T = typename PayT<PAY>::T;
     const uint32_t P = sp.P();
     if (P <= kStagedMaxP) {
-        size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint16_t);
+        size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint32_t);
         auto kern = k_part_scatter_staged<PAY>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -351,7 +349,7 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     {
         const bool staged = P <= kStagedMaxP;
         size_t ssz = payload == PAY_PAIR ? sizeof(uint2) : sizeof(uint32_t);
-        size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint16_t)
+        size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint32_t)
                              : P * sizeof(uint32_t);
         const void *kern = staged ? (payload == PAY_PAIR ? (const void *)k_part_scatter_staged<PAY_PAIR>
                                                          : (const void *)k_part_scatter_staged<PAY_X>)

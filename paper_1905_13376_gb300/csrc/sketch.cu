@@ -89,7 +89,7 @@ uint32_t hll_estimate(const std::vector<unsigned int> &regs) {
 }  // namespace
 
 size_t sketch_workspace_bytes() {
-    return align256(hll_registers() * 4 + 16) + align256(kSample * 4 + 16) +
+    return align256(hll_scratch_registers(256) * 4 + 16) + align256(kSample * 4 + 16) +
            align256(kSample * 8 + 16);
 }
 
@@ -97,7 +97,8 @@ mwj_status compute_features(mwj_ctx *ctx, int kind, const mwj_rel &R, const mwj_
                             const mwj_rel &T, void *ws, size_t ws_bytes, cudaStream_t st, float *f) {
     if (ws_bytes < sketch_workspace_bytes() || !ws) return fail(ctx, MWJ_ERR_WORKSPACE, "sketch workspace");
     unsigned int *regs = (unsigned int *)ws;
-    int32_t *samp = (int32_t *)((char *)ws + align256(hll_registers() * 4 + 16));
+    if (ctx->dev.num_sms > 256) return fail(ctx, MWJ_ERR_UNIMPLEMENTED, "more than 256 SMs");
+    int32_t *samp = (int32_t *)((char *)ws + align256(hll_scratch_registers(256) * 4 + 16));
     unsigned long long *deg =
         (unsigned long long *)((char *)samp + align256(kSample * 4 + 16));
     const int sms = ctx->dev.num_sms;

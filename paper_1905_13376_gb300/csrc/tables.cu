@@ -404,8 +404,19 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
         }
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < HLL_M; j += BT)
-        if (r[j]) atomicMax(&regs[j], r[j]);
+    // this CTA's registers; the size kernel takes the maximum over CTAs
+    for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) regs[(size_t)blockIdx.x * HLL_M + j] = r[j];
+}
+
+constexpr int HLL_CTAS_PER_SM = 4;
+
+// regs[0..HLL_M) = max over the rows of regs[ctas][HLL_M]
+__global__ void k_hll_merge(unsigned int *__restrict__ regs, uint32_t ctas) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= HLL_M) return;
+    unsigned int m = 0;
+    for (uint32_t c = 0; c < ctas; ++c) m = max(m, regs[(size_t)c * HLL_M + j]);
+    regs[j] = m;
 }
 
 // estimate -> table of 2^k >= 4 x estimate slots (at most `reserve`)
@@ -453,21 +464,25 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
                                                        const uint32_t *__restrict__ meta, DevStatus *st) {
     const uint32_t mask = meta[0];
     const bool vec = ((uintptr_t)keys & 15) == 0;
-    const uint32_t stride = gridDim.x * BT * 8;
-    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * 8; i < n; i += stride) {
-        int32_t v[8];
-        if (vec && i + 7 < n) {
-            int4 a = __ldg((const int4 *)(keys + i));
-            int4 b = __ldg((const int4 *)(keys + i + 4));
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    constexpr uint32_t K = 8;
+    const uint32_t stride = gridDim.x * BT * K;
+    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * K; i < n; i += stride) {
+        int32_t v[K];
+        if (vec && i + K - 1 < n) {
+#pragma unroll
+            for (uint32_t q = 0; q < K / 4; ++q) {
+                int4 a = __ldg((const int4 *)(keys + i) + q);
+                v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
+            for (uint32_t k = 0; k < K; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
         }
-        const uint32_t m = min(8u, n - i);
+        const uint32_t m = min(K, n - i);
         uint32_t cur = (uint32_t)v[0], run = 1;
-        for (uint32_t k = 1; k < m; ++k) {
+#pragma unroll
+        for (uint32_t k = 1; k < K; ++k) {
+            if (k >= m) break;
             if ((uint32_t)v[k] == cur) {
                 ++run;
             } else {
@@ -486,11 +501,19 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
                                 DevStatus *status, int num_sms, cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
     const uint32_t nn = (uint32_t)n;
+    const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
     if (nn > 0) {
-        ProfScope ps_("t_hll", st);
-        k_hll<<<num_sms * 2, BT, 0, st>>>(keys, nn, seed, hll_regs);
+        {
+            ProfScope ps_("t_hll", st);
+            k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs);
+        }
+        {
+            ProfScope ps_("t_hll_merge", st);
+            k_hll_merge<<<(HLL_M + 255) / 256, 256, 0, st>>>(hll_regs, ctas);
+        }
+    } else if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) {
+        return e;
     }
     {
         ProfScope ps_("t_size", st);
@@ -502,8 +525,9 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
     }
     if (nn > 0) {
         ProfScope ps_("t_insert", st);
-        k_tinsert_direct<<<num_sms * 4, BT, 0, st>>>(keys, nn, seed, (unsigned long long *)tbl, meta,
-                                                      status);
+        const uint32_t groups = (nn + 8 * BT - 1) / (8 * BT);
+        const uint32_t grid = groups < (uint32_t)num_sms * 4 ? groups : (uint32_t)num_sms * 4;
+        k_tinsert_direct<<<grid, BT, 0, st>>>(keys, nn, seed, (unsigned long long *)tbl, meta, status);
     }
     return cudaGetLastError();
 }
@@ -513,12 +537,20 @@ uint32_t hll_registers() { return HLL_M; }
 cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *regs, int num_sms,
                      cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
     if (n > 0) {
-        ProfScope ps_("sketch_hll", st);
-        k_hll<<<num_sms * 2, BT, 0, st>>>(keys, (uint32_t)n, seed, regs);
+        const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
+        {
+            ProfScope ps_("sketch_hll", st);
+            k_hll<<<ctas, BT, 0, st>>>(keys, (uint32_t)n, seed, regs);
+        }
+        ProfScope ps_("sketch_hll_merge", st);
+        k_hll_merge<<<(HLL_M + 255) / 256, 256, 0, st>>>(regs, ctas);
+    } else if ((e = cudaMemsetAsync(regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) {
+        return e;
     }
     return cudaGetLastError();
 }
+
+size_t hll_scratch_registers(int num_sms) { return (size_t)num_sms * HLL_CTAS_PER_SM * HLL_M; }
 
 }  // namespace mwj

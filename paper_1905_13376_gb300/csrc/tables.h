@@ -63,12 +63,14 @@ cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32
 
 // One table without partitioning T: a HyperLogLog pass over the keys sizes
 // the table (2^k >= 4 x the estimate, at most reserve_slots), then the keys
-// are inserted directly.  hll_regs: hll_registers() u32; meta: 2 u32.
+// are inserted directly.  hll_regs: hll_scratch_registers(num_sms) u32; meta: 2 u32.
 cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
                                 DevStatus *status, int num_sms, cudaStream_t st);
 uint32_t hll_registers();
-// HyperLogLog registers of keys[0, n) into regs (hll_registers() u32, cleared first)
+size_t hll_scratch_registers(int num_sms);
+// HyperLogLog registers of keys[0, n) into regs[0, hll_registers()); regs must
+// hold hll_scratch_registers(num_sms) u32 (per-CTA registers, then merged)
 cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *regs, int num_sms,
                      cudaStream_t st);
 
