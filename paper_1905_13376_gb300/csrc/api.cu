@@ -338,18 +338,20 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     // one g(C) bucket T is not partitioned: its C table is built directly.
     if (!p.single) {
         PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
+        pt.st = ctx->status;
         e = part_run(T.x, T.y, T.n, pt, p.rows ? PAY_PAIR : PAY_X, p.rows ? (void *)L.Tp : (void *)L.Tk,
                      L.offT, L.pscratch, L.pscratch_bytes, ctx->dev.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");
     }
     PartSpec ps{0, sd.B, p.I, p.J > 1 ? 1 : -1, sd.C, p.J};
+    ps.st = ctx->status;
     e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
     PartSpec pr{1, sd.B, p.I, -1, 0, 1};
+    pr.st = ctx->status;
     if (out->mode == MWJ_COUNT_GROUP_BY_A) {   // every a of R must lie in the group-by domain
         pr.dom = (uint32_t)out->a_domain;
-        pr.st = ctx->status;
     }
     e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);

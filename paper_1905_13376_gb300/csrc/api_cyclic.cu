@@ -159,18 +159,18 @@ extern "C" mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_r
         return cuda_fail(ctx, e, "memset group_counts");
     // Fig. 3: R by (H(a), G(b)), S by (G(b), F(c)), T by (F(c), H(a))
     PartSpec pr{0, sd.A, p.x, 1, sd.B, p.y};
-    if (out->mode == MWJ_COUNT_GROUP_BY_A) {
-        pr.dom = (uint32_t)out->a_domain;
-        pr.st = ctx->status;
-    }
+    pr.st = ctx->status;
+    if (out->mode == MWJ_COUNT_GROUP_BY_A) pr.dom = (uint32_t)out->a_domain;
     e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
     PartSpec ps{0, sd.B, p.y, 1, sd.C, p.z};
+    ps.st = ctx->status;
     e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
     PartSpec pt{0, sd.C, p.z, 1, sd.A, p.x};
+    pt.st = ctx->status;
     e = part_run(T.x, T.y, T.n, pt, PAY_PAIR, L.Tp, L.offT, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(KT) k_join2_lin(const int32_t *__restrict__ Ia
         unsigned long long v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            ts[k] = mix32((uint32_t)cv[k] ^ T.seed_slot) & tmask;
+            ts[k] = slot_hash((uint32_t)cv[k], T.seed_slot) & tmask;
             v[k] = (k < (int)m) ? __ldg((const unsigned long long *)(T.img + ts[k])) : kEmpty64;
         }
         int32_t cur = 0;
@@ -630,22 +630,23 @@ extern "C" mwj_status mwj_cascade_join(mwj_ctx *ctx, int kind, mwj_rel R, mwj_re
 
     // join 1 inputs: R and S by H(B)
     PartSpec pr{1, sd.B, p.I1, -1, 0, 1};
-    if (out->mode == MWJ_COUNT_GROUP_BY_A) {
-        pr.dom = (uint32_t)out->a_domain;
-        pr.st = ctx->status;
-    }
+    pr.st = ctx->status;
+    if (out->mode == MWJ_COUNT_GROUP_BY_A) pr.dom = (uint32_t)out->a_domain;
     if ((e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes, sms,
                       st)) != cudaSuccess)
         return cuda_fail(ctx, e, "partition R");
     PartSpec ps{0, sd.B, p.I1, -1, 0, 1};
+    ps.st = ctx->status;
     if ((e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes, sms,
                       st)) != cudaSuccess)
         return cuda_fail(ctx, e, "partition S");
     // join 2's T side
     TImg timg{};
     PartSpec p2{0, sd.C ^ 0x5bd1e995u, p.P2a, 1, sd.A ^ 0x5bd1e995u, p.P2b};
+    p2.st = ctx->status;
     if (kind == MWJ_LINEAR) {
         PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
+        pt.st = ctx->status;
         e = part_run(T.x, T.y, T.n, pt, rows ? PAY_PAIR : PAY_X, rows ? (void *)L.Tp : (void *)L.Tk,
                      L.offT, L.pscratch, L.pscratch_bytes, sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");

@@ -131,7 +131,7 @@ __device__ __forceinline__ int build_all(const uint2 *__restrict__ Rp, uint32_t 
                 slot = tbl_insert(keys, mask, t.y, seed, &fresh);
             } else {
                 slot = -1;
-                uint32_t s = mix32(t.y ^ seed) & mask;
+                uint32_t s = slot_hash(t.y, seed) & mask;
                 for (int it = 0; it < 32; ++it) {
                     uint32_t q = keys[s];
                     if (q == t.y) { slot = (int)s; break; }
@@ -218,7 +218,7 @@ __device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const u
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             if (k < (int)n && sl[k] >= 0) {
-                ts[k] = mix32(t[k].y ^ T.seed_slot) & tmask;
+                ts[k] = slot_hash(t[k].y, T.seed_slot) & tmask;
                 v[k] = __ldg((const unsigned long long *)(T.img + ts[k]));
             }
         }

@@ -138,16 +138,16 @@ extern "C" mwj_status mwj_join3_linear_noalloc(mwj_rel R, mwj_rel S, mwj_rel T,
         cudaMemsetAsync(out->group_counts, 0, sizeof(int64_t) * (size_t)out->a_domain, st) != cudaSuccess)
         return MWJ_ERR_CUDA;
     PartSpec pt{0, sd.C, JT, -1, 0, 1};
+    pt.st = ds.status;
     if (part_run(T.x, T.y, T.n, pt, PAY_X, Tk, offT, pscratch, psb, ds.num_sms, st) != cudaSuccess)
         return MWJ_ERR_CUDA;
     PartSpec pS{0, sd.B, I, J > 1 ? 1 : -1, sd.C, J};
+    pS.st = ds.status;
     if (part_run(S.x, S.y, S.n, pS, PAY_PAIR, Sp, offS, pscratch, psb, ds.num_sms, st) != cudaSuccess)
         return MWJ_ERR_CUDA;
     PartSpec pr{1, sd.B, I, -1, 0, 1};
-    if (out->mode == MWJ_COUNT_GROUP_BY_A) {
-        pr.dom = (uint32_t)out->a_domain;
-        pr.st = ds.status;
-    }
+    pr.st = ds.status;
+    if (out->mode == MWJ_COUNT_GROUP_BY_A) pr.dom = (uint32_t)out->a_domain;
     if (part_run(R.x, R.y, R.n, pr, PAY_PAIR, Rp, offR, pscratch, psb, ds.num_sms, st) != cudaSuccess)
         return MWJ_ERR_CUDA;
     cudaError_t e = single ? single_table_build(Tk, offT, JT, sd.slot2, ekey, ecnt, ecount, meta, img,

@@ -160,44 +160,101 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
     uint32_t *off = cnt + P;                             // P: tile offsets
     T *stage = (T *)(smem + align256(3 * P * sizeof(uint32_t)));   // TILE
     uint32_t *gpos = (uint32_t *)(stage + TILE);         // TILE: output position of each staged tuple
+    int32_t *xin = (int32_t *)(gpos + TILE);             // TILE: the tile's x column (bulk copy)
+    int32_t *yin = xin + TILE;                           // TILE: its y column
     __shared__ uint32_t scan_scratch[33];
+    __shared__ __align__(8) unsigned long long tile_bar;
 
     const uint32_t G = gridDim.x;
     for (uint32_t b = threadIdx.x; b < P; b += PT) cur[b] = scanned[(size_t)b * G + blockIdx.x];
     Chunk c = cta_chunk(n, tiles_per_cta);
+    // tiles start at multiples of TILE, so with 16-byte aligned columns every
+    // tile's first 4*floor(tn/4) values can be bulk-copied; the last few
+    // values of a ragged final tile are read directly
     const bool vec = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    const bool same = (x == y);
     // entries of the per-thread scan over P
     const uint32_t per = (P + PT - 1) / PT;
+    auto issue = [&](uint32_t t0) {
+        const uint32_t tn = min((uint32_t)TILE, c.end - t0);
+        const uint32_t bulk = (tn & ~3u) * 4u;   // bytes, multiple of 16
+        if (bulk == 0) return;
+        fence_proxy_async();
+        mbar_expect_tx(&tile_bar, same ? bulk : 2 * bulk);
+        bulk_copy_g2s(xin, x + t0, bulk, &tile_bar);
+        if (!same) bulk_copy_g2s(yin, y + t0, bulk, &tile_bar);
+    };
+    uint32_t fills = 0;   // completed phases of tile_bar (same in every thread)
+    if (vec) {
+        if (threadIdx.x == 0) {
+            mbar_init(&tile_bar, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && c.begin < c.end) issue(c.begin);
+    }
 
     for (uint32_t t0 = c.begin; t0 < c.end; t0 += TILE) {
         const uint32_t tn = min((uint32_t)TILE, c.end - t0);
         for (uint32_t b = threadIdx.x; b < P; b += PT) cnt[b] = 0;
-        __syncthreads();
+        const bool staged_in = vec && (tn & ~3u) > 0;
+        bool ok = true;
+        if (staged_in) {
+            ok = mbar_wait_bounded(&tile_bar, fills & 1u, 1u << 24);
+            ++fills;
+        }
+        if (__syncthreads_or(!ok)) {
+            // the tile's copy did not land in time: record it and stop (its
+            // data would not match the histogram, so nothing may be written)
+            if (threadIdx.x == 0) {
+                if (sp.st) set_status(sp.st, MWJ_ERR_TIMEOUT, (long long)blockIdx.x);
+                mbar_wait_bounded(&tile_bar, (fills - 1u) & 1u, 1u << 24);
+            }
+            __syncthreads();
+            return;
+        }
         uint32_t bk[IPT], rk[IPT];
         T pv[IPT];
+        int32_t xs8[IPT], ys8[IPT];
         // thread t handles tuples t0 + 4*t + {0..3} and t0 + 2048 + 4*t + {0..3}
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            uint32_t li = (uint32_t)h * (TILE / 2) + threadIdx.x * 4;
-            uint32_t gi = t0 + li;
-            int32_t xs[4], ys[4];
-            if (vec && li + 3 < tn) {
-                int4 xv = __ldg((const int4 *)(x + gi));
-                int4 yv = __ldg((const int4 *)(y + gi));
-                xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
-                ys[0] = yv.x; ys[1] = yv.y; ys[2] = yv.z; ys[3] = yv.w;
-            } else {
+            const uint32_t li = (uint32_t)h * (TILE / 2) + threadIdx.x * 4;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    xs[k] = (li + k < tn) ? __ldg(x + gi + k) : 0;
-                    ys[k] = (li + k < tn) ? __ldg(y + gi + k) : 0;
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t l = li + k;
+                int32_t xv = 0, yv = 0;
+                if (l < tn) {
+                    if (staged_in && l < (tn & ~3u)) {
+                        xv = xin[l];
+                        yv = same ? xv : yin[l];
+                    } else {
+                        xv = __ldg(x + t0 + l);
+                        yv = __ldg(y + t0 + l);
+                    }
                 }
+                xs8[h * 4 + k] = xv;
+                ys8[h * 4 + k] = yv;
+            }
+        }
+        if (staged_in) {
+            __syncthreads();   // every thread has its values: the buffers are free
+            if (threadIdx.x == 0 && t0 + TILE < c.end) issue(t0 + TILE);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t li = (uint32_t)h * (TILE / 2) + threadIdx.x * 4;
+            int32_t xs[4], ys[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                xs[k] = xs8[h * 4 + k];
+                ys[k] = ys8[h * 4 + k];
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 int j = h * 4 + k;
                 if (li + k < tn) {
-                    if (sp.dom && (uint32_t)xs[k] >= sp.dom) set_status(sp.st, MWJ_ERR_DOMAIN, xs[k]);
+                    if (sp.dom && (uint32_t)xs[k] >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xs[k]);
                     bk[j] = bucket_tuple(xs[k], ys[k], sp);
                     rk[j] = atomicAdd(&cnt[bk[j]], 1u);
                     pv[j] = make_pay<PAY>(xs[k], ys[k]);
@@ -252,7 +309,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_direct(
     Chunk c = cta_chunk(n, tiles_per_cta);
     for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
         int32_t xv = __ldg(x + i), yv = __ldg(y + i);
-        if (sp.dom && (uint32_t)xv >= sp.dom) set_status(sp.st, MWJ_ERR_DOMAIN, xv);
+        if (sp.dom && (uint32_t)xv >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xv);
         uint32_t b = bucket_tuple(xv, yv, sp);
         uint32_t p = atomicAdd(&cur[b], 1u);
         out[p] = make_pay<PAY>(xv, yv);
@@ -306,7 +363,8 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
     using T = typename PayT<PAY>::T;
     const uint32_t P = sp.P();
     if (P <= kStagedMaxP) {
-        size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint32_t);
+        size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint32_t) +
+                      2 * TILE * sizeof(int32_t);
         auto kern = k_part_scatter_staged<PAY>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -349,7 +407,8 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     {
         const bool staged = P <= kStagedMaxP;
         size_t ssz = payload == PAY_PAIR ? sizeof(uint2) : sizeof(uint32_t);
-        size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint32_t)
+        size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint32_t) +
+                                   2 * TILE * sizeof(int32_t)
                              : P * sizeof(uint32_t);
         const void *kern = staged ? (payload == PAY_PAIR ? (const void *)k_part_scatter_staged<PAY_PAIR>
                                                          : (const void *)k_part_scatter_staged<PAY_X>)

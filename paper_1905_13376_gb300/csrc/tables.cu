@@ -56,7 +56,7 @@ __device__ __forceinline__ uint32_t gagg_insert(unsigned long long *tbl, uint32_
 __device__ __forceinline__ void single_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
                                               uint32_t seed, unsigned long long add,
                                               DevStatus *st) {
-    uint32_t s = mix32(k ^ seed) & mask;
+    uint32_t s = slot_hash(k, seed) & mask;
     const unsigned long long fresh = (add << 32) | (unsigned long long)k;
     for (uint32_t it = 0; it <= mask; ++it) {
         unsigned long long v = tbl[s];
