@@ -382,6 +382,7 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     g.rowcount = L.rowcount;
     g.st = ctx->status;
     g.spin_limit = (uint32_t)(ctx->spin_limit < (1ll << 24) ? ctx->spin_limit : (1ll << 24));
+    g.build_s = lin_build_s(R.n, S.n);
     int mode = out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0;
     if ((e = lin_agg_launch(g, mode, st)) != cudaSuccess) return cuda_fail(ctx, e, "linear probe");
     if (p.rows) {

@@ -93,7 +93,7 @@ __device__ __forceinline__ uint32_t seg_bucket(int32_t x, int32_t y, const PartS
 
 __device__ __forceinline__ void ttab_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
                                             uint32_t seed, DevStatus *st) {
-    uint32_t s = slot_hash(k, seed) & mask;
+    uint32_t s = slot_of(k, seed, mask);
     const unsigned long long fresh = (1ull << 32) | (unsigned long long)k;
     for (uint32_t it = 0; it <= mask; ++it) {
         unsigned long long v = tbl[s];
@@ -212,7 +212,7 @@ union JoinSmem {
 
 __device__ __forceinline__ uint32_t t_deg(const unsigned long long *tbl, uint32_t mask, uint32_t c,
                                           uint32_t seed) {
-    uint32_t s = slot_hash(c, seed) & mask;
+    uint32_t s = slot_of(c, seed, mask);
     for (uint32_t it = 0; it <= mask; ++it) {
         unsigned long long v = __ldg(tbl + s);
         if (v == kEmpty64) return 0;

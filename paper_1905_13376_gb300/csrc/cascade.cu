@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(KT) k_join2_lin(const int32_t *__restrict__ Ia
         unsigned long long v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            ts[k] = slot_hash((uint32_t)cv[k], T.seed_slot) & tmask;
+            ts[k] = slot_of((uint32_t)cv[k], T.seed_slot, tmask);
             v[k] = (k < (int)m) ? __ldg((const unsigned long long *)(T.img + ts[k])) : kEmpty64;
         }
         int32_t cur = 0;

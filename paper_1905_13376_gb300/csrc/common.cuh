@@ -3,8 +3,8 @@
 // Hashing (Section 4, "robust hash functions"; Fig. 2's two hash levels):
 // every attribute has its own seed; the top-level bucket of a key is
 // fastrange(mix32(key ^ seed), P) so that any bucket count P works, and the
-// slot of a key inside a power-of-two table uses slot_hash (a multiply and
-// an xor-shift, cheaper than mix32) with a different seed.
+// slot of a key inside a power-of-two table uses slot_of (Fibonacci hashing:
+// one multiply, cheaper than mix32) with a different seed.
 #pragma once
 
 #include <cstdint>
@@ -44,11 +44,12 @@ __host__ __device__ __forceinline__ uint32_t fastrange(uint32_t h, uint32_t n) {
     return (uint32_t)(((uint64_t)h * (uint64_t)n) >> 32);
 }
 
-// slot hash of power-of-two tables: Fibonacci multiplication, then the high
-// half folded into the low bits the mask keeps
-__host__ __device__ __forceinline__ uint32_t slot_hash(uint32_t k, uint32_t seed) {
-    uint32_t h = (k ^ seed) * 0x9E3779B1u;
-    return h ^ (h >> 16);
+// Home slot of key k in a table of mask + 1 = 2^L slots: Fibonacci hashing,
+// the top L bits of (k ^ seed) * floor(2^32 / phi).  The top bits of the
+// product depend on every bit of the key (the low bits only on the key's low
+// bits), and a run of consecutive keys lands spread evenly over the table.
+__host__ __device__ __forceinline__ uint32_t slot_of(uint32_t k, uint32_t seed, uint32_t mask) {
+    return fastrange((k ^ seed) * 0x9E3779B1u, mask + 1u);
 }
 
 __host__ __device__ __forceinline__ uint32_t bucket_of(int32_t key, uint32_t seed, uint32_t P) {
@@ -81,7 +82,7 @@ inline Seeds make_seeds(uint32_t s) {
 __device__ __forceinline__ int tbl_find(const uint32_t *keys, uint32_t mask, uint32_t k,
                                         uint32_t seed) {
     if (k == kEmptyKey) return keys[mask + 1] ? (int)(mask + 1) : -1;
-    uint32_t s = slot_hash(k, seed) & mask;
+    uint32_t s = slot_of(k, seed, mask);
     for (uint32_t it = 0; it <= mask; ++it) {   // bounded: a full table ends the search
         uint32_t q = keys[s];
         if (q == k) return (int)s;
@@ -103,7 +104,7 @@ __device__ __forceinline__ int tbl_insert(uint32_t *keys, uint32_t mask, uint32_
         }
         return (int)(mask + 1);
     }
-    uint32_t s = slot_hash(k, seed) & mask;
+    uint32_t s = slot_of(k, seed, mask);
     for (uint32_t it = 0; it <= mask; ++it) {
         uint32_t q = keys[s];
         if (q == k) return (int)s;

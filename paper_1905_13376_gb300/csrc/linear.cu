@@ -34,11 +34,13 @@ __device__ __forceinline__ void tbl_clear(uint32_t *keys, uint32_t cap) {
     if (threadIdx.x == 0) keys[cap] = 0u;
 }
 
-// Insert R tuples [pos, ...) in rounds of round_tuples(cap) tuples while the
-// table stays at most 3/4 full (so it is never full) and the chunk stays
-// within max_tuples; returns the chunk end, which is always past pos.
-// on_insert(slot, tuple) runs for every inserted tuple.  Ends with a barrier.
-template <typename F>
+// Insert tuples [pos, ...) of a bucket, keyed by their second column (R's
+// b) or, with KEY_X, their first (S's b), in rounds of round_tuples(cap)
+// tuples while the table stays at most 3/4 full (so it is never full) and
+// the chunk stays within max_tuples; returns the chunk end, which is always
+// past pos.  on_insert(slot, tuple) runs for every inserted tuple.  Ends
+// with a barrier.
+template <bool KEY_X = false, typename F>
 __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, uint32_t pos,
                                                 uint32_t r1, uint32_t *keys, uint32_t cap,
                                                 uint32_t seed, uint32_t max_tuples,
@@ -59,7 +61,7 @@ __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, ui
             if (li < rt && idx < r1) {
                 uint2 t = __ldg(Rp + idx);
                 bool fresh;
-                int slot = tbl_insert(keys, mask, t.y, seed, &fresh);
+                int slot = tbl_insert(keys, mask, KEY_X ? t.x : t.y, seed, &fresh);
                 if (slot < 0) {
                     set_status(st, MWJ_ERR_CHECK, 1);
                     continue;
@@ -73,6 +75,27 @@ __device__ __forceinline__ uint32_t build_chunk(const uint2 *__restrict__ Rp, ui
         cend += rt;
     }
     return cend < r1 ? cend : r1;
+}
+
+// Insert-or-find with a probe sequence of at most 32 slots (optimistic
+// passes); -1 when the sequence ran out, which the caller treats as a failed
+// pass.  The key kEmptyKey lives in the extra slot mask + 1.
+__device__ __forceinline__ int tbl_insert32(uint32_t *keys, uint32_t mask, uint32_t k, uint32_t seed,
+                                            bool *fresh) {
+    if (k == kEmptyKey) return tbl_insert(keys, mask, k, seed, fresh);
+    *fresh = false;
+    uint32_t s = slot_of(k, seed, mask);
+    for (int it = 0; it < 32; ++it) {
+        uint32_t q = keys[s];
+        if (q == k) return (int)s;
+        if (q == kEmptyKey) {
+            uint32_t old = atomicCAS(&keys[s], kEmptyKey, k);
+            if (old == kEmptyKey) { *fresh = true; return (int)s; }
+            if (old == k) return (int)s;
+        }
+        s = (s + 1) & mask;
+    }
+    return -1;
 }
 
 // Bulk-copy pipeline of two shared-memory buffers, each with a "full"
@@ -125,24 +148,8 @@ __device__ __forceinline__ int build_all(const uint2 *__restrict__ Rp, uint32_t 
             const uint32_t gi = base + j;
             if (gi < pos || gi >= r1) continue;
             const uint2 t = src[j];
-            int slot;
-            bool fresh = false;
-            if (t.y == kEmptyKey) {
-                slot = tbl_insert(keys, mask, t.y, seed, &fresh);
-            } else {
-                slot = -1;
-                uint32_t s = slot_hash(t.y, seed) & mask;
-                for (int it = 0; it < 32; ++it) {
-                    uint32_t q = keys[s];
-                    if (q == t.y) { slot = (int)s; break; }
-                    if (q == kEmptyKey) {
-                        uint32_t old = atomicCAS(&keys[s], kEmptyKey, t.y);
-                        if (old == kEmptyKey) { slot = (int)s; fresh = true; break; }
-                        if (old == t.y) { slot = (int)s; break; }
-                    }
-                    s = (s + 1) & mask;
-                }
-            }
+            bool fresh;
+            const int slot = tbl_insert32(keys, mask, t.y, seed, &fresh);
             if (slot < 0) {
                 failed = true;
                 break;
@@ -207,39 +214,43 @@ __device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint
     }
 }
 
-// deg_T of the NB C values of a batch: the first probe of every tuple is
-// issued before any is consumed (one L2 round trip for the whole batch in
-// the common case).
+// First probes of T's single table (T.J == 0) for the C values of a batch,
+// all issued before any is consumed: one L2 round trip for the batch in the
+// common case.  use[k] selects the tuples that need deg_T.
+__device__ __forceinline__ void t_issue(const TImg &T, uint32_t tmask, const uint2 (&t)[NB],
+                                        const bool (&use)[NB], uint32_t (&ts)[NB],
+                                        unsigned long long (&v)[NB]) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (use[k]) {
+            ts[k] = slot_of(t[k].y, T.seed_slot, tmask);
+            v[k] = __ldg((const unsigned long long *)(T.img + ts[k]));
+        }
+    }
+}
+
+// deg_T(c) from the first probe (slot s, value x) of c in the single table.
+__device__ __forceinline__ uint32_t t_resolve(const TImg &T, uint32_t tmask, uint32_t c, uint32_t s,
+                                              unsigned long long x) {
+    for (uint32_t it = 0; it < tmask && x != kEmpty64 && (uint32_t)x != c; ++it) {
+        s = (s + 1) & tmask;
+        x = __ldg((const unsigned long long *)(T.img + s));
+    }
+    return (x == kEmpty64 || (uint32_t)x != c) ? 0u : (uint32_t)(x >> 32);
+}
+
+// deg_T of the C values of the batch tuples with use[k] (0 for the others).
 __device__ __forceinline__ void t_degrees(const TImg &T, uint32_t tmask, const uint2 (&t)[NB],
-                                          const int (&sl)[NB], uint32_t n, uint32_t (&dT)[NB]) {
+                                          const bool (&use)[NB], uint32_t (&dT)[NB]) {
     if (T.J == 0) {
         uint32_t ts[NB];
         unsigned long long v[NB];
+        t_issue(T, tmask, t, use, ts, v);
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            if (k < (int)n && sl[k] >= 0) {
-                ts[k] = slot_hash(t[k].y, T.seed_slot) & tmask;
-                v[k] = __ldg((const unsigned long long *)(T.img + ts[k]));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            dT[k] = 0;
-            if (k < (int)n && sl[k] >= 0) {
-                unsigned long long x = v[k];
-                uint32_t s = ts[k];
-                for (uint32_t it = 0; it < tmask && x != kEmpty64 && (uint32_t)x != t[k].y; ++it) {
-                    s = (s + 1) & tmask;
-                    x = __ldg((const unsigned long long *)(T.img + s));
-                }
-                if ((uint32_t)x != t[k].y) x = kEmpty64;
-                dT[k] = (x == kEmpty64) ? 0u : (uint32_t)(x >> 32);
-            }
-        }
+        for (int k = 0; k < NB; ++k) dT[k] = use[k] ? t_resolve(T, tmask, t[k].y, ts[k], v[k]) : 0u;
     } else {
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            dT[k] = (k < (int)n && sl[k] >= 0) ? timg_deg(T, (int32_t)t[k].y) : 0u;
+        for (int k = 0; k < NB; ++k) dT[k] = use[k] ? timg_deg(T, (int32_t)t[k].y) : 0u;
     }
 }
 
@@ -332,8 +343,11 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
                     sl[k] = (k < (int)n) ? tbl_find(keys, mask, t[k].x, g.seed_slot) : -1;
+                bool use[NB];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) use[k] = sl[k] >= 0;
                 uint32_t dT[NB];
-                t_degrees(g.t, tmask, t, sl, n, dT);
+                t_degrees(g.t, tmask, t, use, dT);
                 if (MODE == 0) {
 #pragma unroll
                     for (int k = 0; k < NB; ++k)
@@ -384,6 +398,160 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
                     if (have) atomicAdd(g.cnt + cur, run);
                 });
             }
+            __syncthreads();   // the table is rebuilt for the next chunk
+            pos = cend;
+        }
+    }
+    unsigned long long tot = block_sum_u64(acc, red);
+    if (threadIdx.x == 0) {
+        if (tot) atomicAdd(g.total, tot);
+        if (g.rowcount) g.rowcount[i] = tot;
+    }
+}
+
+// The same two aggregates with S_i as the on-chip side.  The B-keyed table
+// of CTA i gathers w(b) = sum of deg_T(c) over the tuples (b, c) of S_i while
+// S_i streams in once; then R_i streams past it once, adding w(b) to total
+// and to cnt[a] for every (a, b).  Each R tuple is read and hashed once
+// (the R-side kernel above reads and hashes it twice, to build and to
+// flush); in exchange every S tuple pays its T lookup whether or not its b
+// occurs in R_i.  When S_i holds more distinct B values than the table
+// keeps, S_i is taken in chunks, each followed by its own pass over R_i.
+template <int MODE>
+__global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t cap = 1u << g.cap_log2;
+    const size_t arr = align256((cap + 1) * sizeof(uint32_t));
+    uint32_t *keys = (uint32_t *)smem;
+    uint32_t *wlo = (uint32_t *)(smem + arr);
+    uint32_t *whi = (uint32_t *)(smem + 2 * arr);
+    __shared__ uint32_t nd, bad;
+    __shared__ unsigned long long red[32];
+
+    const uint32_t i = blockIdx.x;
+    const uint32_t r0 = g.offR[i], r1 = g.offR[i + 1];
+    const uint32_t s0 = g.offS[(size_t)i * g.JS], s1 = g.offS[(size_t)(i + 1) * g.JS];
+    const uint32_t tmask = (g.t.J == 0) ? __ldg(g.t.meta) : 0u;
+    const uint32_t mask = cap - 1;
+    unsigned long long acc = 0;
+
+    auto clear = [&]() {   // ends with a barrier
+        tbl_clear(keys, cap);
+        for (uint32_t s = threadIdx.x; s <= cap; s += LT) {
+            wlo[s] = 0u;
+            whi[s] = 0u;
+        }
+        if (threadIdx.x == 0) {
+            nd = 0;
+            bad = 0;
+        }
+        __syncthreads();
+    };
+    // w[slot] += v for the batch's (slot, v), runs of equal slots merged
+    auto add_w = [&](const int (&sl)[NB], const uint32_t (&dT)[NB]) {
+        int cur = -1;
+        unsigned long long run = 0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (sl[k] < 0 || !dT[k]) continue;
+            if (sl[k] == cur) {
+                run += dT[k];
+            } else {
+                if (cur >= 0) add_u64_split(&wlo[cur], &whi[cur], run);
+                cur = sl[k];
+                run = dT[k];
+            }
+        }
+        if (cur >= 0) add_u64_split(&wlo[cur], &whi[cur], run);
+    };
+
+    if (r0 < r1 && s0 < s1) {
+        for (uint32_t pos = s0; pos < s1;) {
+            clear();
+            uint32_t cend = s1;
+            bool ok = false;
+            if (pos == s0) {
+                // optimistic pass over all of S_i, inserts of at most 32 probes
+                uint32_t fresh_n = 0;
+                stream_batches(g.Sp, s0, s1, [&](const uint2 (&t)[NB], uint32_t n) {
+                    if (*(volatile uint32_t *)&bad) return;   // the pass has failed already
+                    bool use[NB];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) use[k] = k < (int)n;
+                    uint32_t ts[NB];
+                    unsigned long long v[NB];
+                    if (g.t.J == 0) t_issue(g.t, tmask, t, use, ts, v);   // in flight during the inserts
+                    int sl[NB];
+                    bool failed = false;
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        sl[k] = -1;
+                        if (!use[k]) continue;
+                        if (k > 0 && t[k].x == t[k - 1].x) {   // S arrives grouped by b
+                            sl[k] = sl[k - 1];
+                            continue;
+                        }
+                        bool fresh;
+                        sl[k] = tbl_insert32(keys, mask, t[k].x, g.seed_slot, &fresh);
+                        fresh_n += fresh;
+                        failed |= sl[k] < 0;
+                    }
+                    if (failed) {
+                        atomicOr(&bad, 1u);
+                        return;
+                    }
+                    uint32_t dT[NB];
+                    if (g.t.J == 0) {
+#pragma unroll
+                        for (int k = 0; k < NB; ++k)
+                            dT[k] = use[k] ? t_resolve(g.t, tmask, t[k].y, ts[k], v[k]) : 0u;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) dT[k] = use[k] ? timg_deg(g.t, (int32_t)t[k].y) : 0u;
+                    }
+                    add_w(sl, dT);
+                });
+                fresh_n = warp_sum(fresh_n);
+                if ((threadIdx.x & 31) == 0 && fresh_n) atomicAdd(&nd, fresh_n);
+                __syncthreads();
+                ok = !bad && nd <= cap - cap / 4;
+                __syncthreads();   // every thread has read nd and bad
+                if (!ok) clear();
+            }
+            if (!ok)   // chunks built in bounded rounds, one T lookup per tuple
+                cend = build_chunk<true>(g.Sp, pos, s1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd, g.st,
+                                         [&](int slot, uint2 t) {
+                                             const uint32_t d = timg_deg(g.t, (int32_t)t.y);
+                                             if (d) add_u64_split(&wlo[slot], &whi[slot], d);
+                                         });
+            // R_i streams past w: total += w(b), cnt[a] += w(b), runs of equal A merged
+            stream_batches(g.Rp, r0, r1, [&](const uint2 (&t)[NB], uint32_t n) {
+                int32_t cur = 0;
+                unsigned long long run = 0;
+                bool have = false;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    if (k >= (int)n) break;
+                    const int slot = tbl_find(keys, mask, t[k].y, g.seed_slot);
+                    if (slot < 0) continue;
+                    const unsigned long long w =
+                        ((unsigned long long)whi[slot] << 32) | (unsigned long long)wlo[slot];
+                    if (!w) continue;
+                    if (MODE == 1) {
+                        if ((uint32_t)t[k].x >= (uint32_t)g.a_domain) continue;
+                        if (have && (int32_t)t[k].x == cur) {
+                            run += w;
+                        } else {
+                            if (have) atomicAdd(g.cnt + cur, run);
+                            cur = (int32_t)t[k].x;
+                            run = w;
+                            have = true;
+                        }
+                    }
+                    acc += w;
+                }
+                if (MODE == 1 && have) atomicAdd(g.cnt + cur, run);
+            });
             __syncthreads();   // the table is rebuilt for the next chunk
             pos = cend;
         }
@@ -501,8 +669,9 @@ __global__ void k_rows_check(const unsigned long long *base, uint32_t I, long lo
 
 }  // namespace
 
-size_t lin_agg_smem(uint32_t cap_log2, int mode) {
+size_t lin_agg_smem(uint32_t cap_log2, int mode, bool build_s) {
     uint32_t cap = 1u << cap_log2;
+    if (build_s) return align256((cap + 1) * 4) * 3;
     return align256((cap + 1) * 4) * (mode == 1 ? 3 : 2) + 2 * RCH * sizeof(uint2);
 }
 
@@ -511,22 +680,25 @@ size_t lin_rows_smem(uint32_t cap_log2, uint32_t max_tuples) {
     return 3 * align256((cap + 1) * 4) + (size_t)max_tuples * 4;
 }
 
+template <typename K>
+static cudaError_t launch_agg(K kernel, const LinArgs &g, size_t smem, const char *name,
+                             cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ProfScope ps_(name, st);
+    kernel<<<g.I, LT, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
 cudaError_t lin_agg_launch(const LinArgs &g, int mode, cudaStream_t st) {
     if (g.I == 0) return cudaSuccess;
-    size_t smem = lin_agg_smem(g.cap_log2, mode);
-    cudaError_t e;
-    if (mode == 1) {
-        e = cudaFuncSetAttribute(k_lin_agg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ProfScope ps_("lin_probe_groupby", st);
-        k_lin_agg<1><<<g.I, LT, smem, st>>>(g);
-    } else {
-        e = cudaFuncSetAttribute(k_lin_agg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ProfScope ps_("lin_probe_count", st);
-        k_lin_agg<0><<<g.I, LT, smem, st>>>(g);
-    }
-    return cudaGetLastError();
+    const size_t smem = lin_agg_smem(g.cap_log2, mode, g.build_s != 0);
+    const char *name = mode == 1 ? "lin_probe_groupby" : "lin_probe_count";
+    if (g.build_s)
+        return mode == 1 ? launch_agg(k_lin_agg_s<1>, g, smem, name, st)
+                         : launch_agg(k_lin_agg_s<0>, g, smem, name, st);
+    return mode == 1 ? launch_agg(k_lin_agg<1>, g, smem, name, st)
+                     : launch_agg(k_lin_agg<0>, g, smem, name, st);
 }
 
 cudaError_t lin_rows_launch(const LinArgs &g, const unsigned long long *base, int32_t *rows,

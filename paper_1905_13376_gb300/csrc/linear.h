@@ -20,9 +20,16 @@ struct LinArgs {
     unsigned long long *rowcount;   // per R bucket (row output, pass 1), or null
     DevStatus *st;
     uint32_t spin_limit;        // polls of a bounded barrier wait before MWJ_ERR_TIMEOUT
+    uint32_t build_s;           // aggregates: 1 = S_i is the on-chip side, 0 = R_i (Algorithm 1)
 };
 
-size_t lin_agg_smem(uint32_t cap_log2, int mode);
+// On-chip side of the aggregate kernels: S_i whenever |S| <= 2 |R|, so that
+// every R tuple is read and hashed once; R_i (Algorithm 1's roles) when S is
+// much larger than R, where the T lookups of S tuples that meet no R tuple
+// would cost more than the second pass over R.
+inline uint32_t lin_build_s(int64_t nR, int64_t nS) { return nS <= 2 * nR ? 1u : 0u; }
+
+size_t lin_agg_smem(uint32_t cap_log2, int mode, bool build_s);
 size_t lin_rows_smem(uint32_t cap_log2, uint32_t max_tuples);
 cudaError_t lin_agg_launch(const LinArgs &g, int mode, cudaStream_t st);
 cudaError_t lin_rows_launch(const LinArgs &g, const unsigned long long *base, int32_t *rows,

@@ -167,6 +167,7 @@ extern "C" mwj_status mwj_join3_linear_noalloc(mwj_rel R, mwj_rel S, mwj_rel T,
     g.rowcount = nullptr;
     g.st = ds.status;
     g.spin_limit = 1u << 24;
+    g.build_s = lin_build_s(R.n, S.n);
     if (lin_agg_launch(g, out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0, st) != cudaSuccess)
         return MWJ_ERR_CUDA;
 

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(ST) k_sample_degrees(const int32_t *__restrict
                                                        unsigned long long *__restrict__ deg) {
     __shared__ uint32_t tk[kSampleSlots + 1];
     __shared__ uint32_t tc[kSampleSlots + 1];
-    __shared__ int32_t slot_of[kSample];
+    __shared__ int32_t slot_at[kSample];
     const uint32_t mask = kSampleSlots - 1;
     for (uint32_t s = threadIdx.x; s <= kSampleSlots; s += ST) {
         tk[s] = (s < kSampleSlots) ? kEmptyKey : 0u;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(ST) k_sample_degrees(const int32_t *__restrict
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < nk; k += ST) {
         bool fresh;
-        slot_of[k] = tbl_insert(tk, mask, (uint32_t)keys[k], seed, &fresh);
+        slot_at[k] = tbl_insert(tk, mask, (uint32_t)keys[k], seed, &fresh);
     }
     __syncthreads();
     for (uint32_t i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) {
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(ST) k_sample_degrees(const int32_t *__restrict
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < nk; k += ST) {
-        int s = slot_of[k];
+        int s = slot_at[k];
         if (s >= 0 && tc[s]) {
             // every sampled key k receives its slot's count once per CTA
             atomicAdd(deg + k, (unsigned long long)tc[s]);

@@ -27,6 +27,10 @@ namespace {
 
 constexpr int BT = 512;
 constexpr uint32_t kAggSlots = 8192;          // shared-memory aggregation table
+// Slots of the single T table per estimated distinct C value: the power of
+// two at or above 4 x the estimate keeps the load between 1/8 and 1/4 (a
+// factor of 2 measured slower: longer probe runs in both insert and lookup).
+constexpr double kSingleTableFactor = 4.0;
 constexpr uint32_t kImgSmemSlots = 8192;      // 64 KB of packed slots (bucket images)
 
 // insert into a global region of arbitrary capacity (fastrange start), adding `add`
@@ -56,7 +60,7 @@ __device__ __forceinline__ uint32_t gagg_insert(unsigned long long *tbl, uint32_
 __device__ __forceinline__ void single_insert(unsigned long long *tbl, uint32_t mask, uint32_t k,
                                               uint32_t seed, unsigned long long add,
                                               DevStatus *st) {
-    uint32_t s = slot_hash(k, seed) & mask;
+    uint32_t s = slot_of(k, seed, mask);
     const unsigned long long fresh = (add << 32) | (unsigned long long)k;
     for (uint32_t it = 0; it <= mask; ++it) {
         unsigned long long v = tbl[s];
@@ -419,8 +423,8 @@ __global__ void k_hll_merge(unsigned int *__restrict__ regs, uint32_t ctas) {
     regs[j] = m;
 }
 
-// estimate -> table of 2^k >= 4 x estimate slots (at most `reserve`)
-__global__ void k_hll_size(const unsigned int *__restrict__ regs, uint64_t reserve,
+// estimate -> table of 2^k >= factor x estimate slots (at most `reserve`)
+__global__ void k_hll_size(const unsigned int *__restrict__ regs, uint64_t reserve, double factor,
                            uint32_t *__restrict__ meta) {
     __shared__ double part[32];
     __shared__ unsigned int zeros[32];
@@ -450,7 +454,7 @@ __global__ void k_hll_size(const unsigned int *__restrict__ regs, uint64_t reser
         double E = (0.7213 / (1.0 + 1.079 / m)) * m * m / S;
         if (E <= 2.5 * m && Z > 0) E = m * log(m / (double)Z);   // small-range correction
         uint64_t cap = 16;
-        while ((double)cap < 4.0 * E && cap < reserve) cap <<= 1;
+        while ((double)cap < factor * E && cap < reserve) cap <<= 1;
         if (cap > reserve) cap = reserve;
         meta[0] = (uint32_t)(cap - 1);
         meta[1] = (uint32_t)E;
@@ -517,7 +521,7 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
     }
     {
         ProfScope ps_("t_size", st);
-        k_hll_size<<<1, 1024, 0, st>>>(hll_regs, reserve_slots, meta);
+        k_hll_size<<<1, 1024, 0, st>>>(hll_regs, reserve_slots, kSingleTableFactor, meta);
     }
     {
         ProfScope ps_("t_clear", st);

@@ -5,8 +5,8 @@
 
 namespace mwj {
 
-// J == 0: one table of (meta[0] + 1) packed (deg << 32 | c) slots, slot hash
-//         slot_hash(c, seed_slot) & meta[0].
+// J == 0: one table of (meta[0] + 1) packed (deg << 32 | c) slots, home slot
+//         slot_of(c, seed_slot, meta[0]).
 // J >= 1: bucket j = bucket_of(c, seed_bucket, J) lives at
 //         img[2*off[j] .. 2*off[j] + cap[j]); with row output start[2*off[j] + slot]
 //         is the first position of c's D values in dlist.
@@ -25,7 +25,7 @@ struct TImg {
 __device__ __forceinline__ uint32_t timg_deg(const TImg &t, int32_t c) {
     if (t.J == 0) {
         const uint32_t mask = __ldg(t.meta);
-        uint32_t s = slot_hash((uint32_t)c, t.seed_slot) & mask;
+        uint32_t s = slot_of((uint32_t)c, t.seed_slot, mask);
         for (uint32_t it = 0; it <= mask; ++it) {
             uint64_t v = __ldg((const unsigned long long *)(t.img + s));
             if (v == kEmpty64) return 0;

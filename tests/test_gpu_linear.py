@@ -97,6 +97,19 @@ def test_many_distinct_keys_in_one_bucket_chunks(ctx):
     check_all_modes(ctx, R, S, T, 1000, shares=(2, 3))
 
 
+@pytest.mark.parametrize("nR,nS", [(20000, 60000), (60000, 20000), (30000, 30000)])
+def test_build_side_and_chunks(ctx, nR, nS):
+    """|S| > 2|R| keeps R_i on chip (Algorithm 1's roles); otherwise S_i is
+    the on-chip side of the aggregates.  With few buckets either side holds
+    more distinct B values than one table, so both run in chunks."""
+    g = np.random.default_rng(nR + 7 * nS)
+    R = (g.integers(0, 500, nR).astype(np.int32), g.integers(0, 40000, nR).astype(np.int32))
+    S = (g.integers(0, 40000, nS).astype(np.int32), g.integers(0, 2000, nS).astype(np.int32))
+    T = (g.integers(0, 2000, 5000).astype(np.int32), g.integers(0, 10, 5000).astype(np.int32))
+    for shares in [(1, 1), (4, 1), (64, 1), (8, 4), (16, 1, 9)]:
+        check_all_modes(ctx, R, S, T, 500, shares=shares, rows=False)
+
+
 def test_skewed_zipf(ctx):
     g = np.random.default_rng(8)
     q = datagen.random_query(g, "linear", size_lo=20000, size_hi=40000, dom_lo=200, dom_hi=2000,
