@@ -157,6 +157,44 @@ __device__ __forceinline__ int64_t img_slot(const uint64_t *img, uint32_t cap, u
     return -1;
 }
 
+// ---------------------------------------------------------------------------
+// Read-once streams.  Relations and partitions pass through the L2 once; an
+// L2 evict_first policy lets them leave before the lookup tables that many
+// CTAs share (T's C table), and L1::no_allocate keeps them out of the L1,
+// which then caches the hot part of those tables.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ int4 ld_stream(const int4 *ptr, uint64_t pol) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream(const uint4 *ptr, uint64_t pol) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_stream(uint2 *ptr, uint2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(ptr), "r"(v.x), "r"(v.y),
+                 "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_stream(uint32_t *ptr, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
     atomicAdd(p, v);
 }

@@ -186,6 +186,7 @@ template <typename F>
 __device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint32_t s0, uint32_t s1,
                                                F &&f) {
     if (s0 >= s1) return;
+    const uint64_t pol = l2_evict_first();
     uint32_t a = s0;
     uint2 t[NB];
     if (a & 1u) {
@@ -195,22 +196,32 @@ __device__ __forceinline__ void stream_batches(const uint2 *__restrict__ p, uint
         }
         ++a;
     }
-    for (uint32_t b = a + NB * threadIdx.x; b < s1; b += NB * LT) {
-        const uint32_t n = min((uint32_t)NB, s1 - b);
-        if (n == NB) {
+    // the next batch's loads are issued before the current batch is handed on
+    auto load = [&](uint32_t b, uint2 (&t)[NB]) {
+        if (b + NB <= s1) {
             const uint4 *q = (const uint4 *)(p + b);
 #pragma unroll
             for (int k = 0; k < NB / 2; ++k) {
-                uint4 u = __ldg(q + k);
+                uint4 u = ld_stream(q + k, pol);
                 t[2 * k] = make_uint2(u.x, u.y);
                 t[2 * k + 1] = make_uint2(u.z, u.w);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < NB; ++k)
-                if (k < (int)n) t[k] = __ldg(p + b + k);
+                if (b + k < s1) t[k] = __ldg(p + b + k);
         }
-        f(t, n);
+    };
+    uint32_t b = a + NB * threadIdx.x;
+    if (b < s1) load(b, t);
+    while (b < s1) {
+        const uint32_t nb = b + NB * LT;
+        uint2 nx[NB];
+        if (nb < s1) load(nb, nx);
+        f(t, min((uint32_t)NB, s1 - b));
+#pragma unroll
+        for (int k = 0; k < NB; ++k) t[k] = nx[k];
+        b = nb;
     }
 }
 

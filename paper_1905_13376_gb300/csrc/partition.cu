@@ -71,16 +71,38 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
     uint32_t *my = WARP_PRIVATE ? hist + (threadIdx.x >> 5) * P : hist;
     Chunk c = cta_chunk(n, tiles_per_cta);
     const bool vec = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    const uint64_t pol = l2_evict_first();
     uint32_t i = c.begin + threadIdx.x * 4;
+    // one atomic per run of equal buckets among 4 consecutive tuples
+    auto count4 = [&](const int4 &xv, const int4 &yv) {
+        const uint32_t b0 = bucket_tuple(xv.x, yv.x, sp), b1 = bucket_tuple(xv.y, yv.y, sp),
+                       b2 = bucket_tuple(xv.z, yv.z, sp), b3 = bucket_tuple(xv.w, yv.w, sp);
+        uint32_t run = 1;
+        if (b1 == b0) ++run; else { atomicAdd(&my[b0], run); run = 1; }
+        if (b2 == b1) ++run; else { atomicAdd(&my[b1], run); run = 1; }
+        if (b3 == b2) ++run; else { atomicAdd(&my[b2], run); run = 1; }
+        atomicAdd(&my[b3], run);
+    };
     if (vec) {
+        // four 16-byte loads in flight per thread before any is consumed
+        constexpr uint32_t U = 4;
+        for (; i + (U - 1) * PT * 4 + 3 < c.end; i += U * PT * 4) {
+            int4 xv[U], yv[U];
+#pragma unroll
+            for (uint32_t u = 0; u < U; ++u) {
+                xv[u] = make_int4(0, 0, 0, 0);
+                yv[u] = make_int4(0, 0, 0, 0);
+                if (USE & 1) xv[u] = ld_stream((const int4 *)(x + i + u * PT * 4), pol);
+                if (USE & 2) yv[u] = ld_stream((const int4 *)(y + i + u * PT * 4), pol);
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < U; ++u) count4(xv[u], yv[u]);
+        }
         for (; i + 3 < c.end; i += PT * 4) {
             int4 xv = make_int4(0, 0, 0, 0), yv = make_int4(0, 0, 0, 0);
-            if (USE & 1) xv = __ldg((const int4 *)(x + i));
-            if (USE & 2) yv = __ldg((const int4 *)(y + i));
-            atomicAdd(&my[bucket_tuple(xv.x, yv.x, sp)], 1u);
-            atomicAdd(&my[bucket_tuple(xv.y, yv.y, sp)], 1u);
-            atomicAdd(&my[bucket_tuple(xv.z, yv.z, sp)], 1u);
-            atomicAdd(&my[bucket_tuple(xv.w, yv.w, sp)], 1u);
+            if (USE & 1) xv = ld_stream((const int4 *)(x + i), pol);
+            if (USE & 2) yv = ld_stream((const int4 *)(y + i), pol);
+            count4(xv, yv);
         }
     }
     for (; i < c.end; i += PT * 4) {
@@ -295,6 +317,177 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
     }
 }
 
+// K3 (P <= kWcMaxP): tile-local counting sort with write combining.  The
+// run of bucket b in a tile is the tuples the CTA carried over from its
+// earlier tiles followed by the tile's own; only whole 32-byte sectors of
+// the run are written and the remainder (less than a sector) is carried on.
+// Apart from the first and the last sector of each CTA's range in a bucket,
+// every output sector is thus written once and whole, within one phase of
+// one tile, so the L2 never has to merge a partly written sector with its
+// DRAM contents (a DRAM read each).
+//
+// Carried tuples always lie in one sector, [gs, gs + carried): either the
+// run completes that sector (then all of them are written, W >= carried)
+// or nothing of the run is written and they stay in their carry slots.
+constexpr uint32_t kWcMaxP = 1024;
+constexpr uint32_t kToCarry = 0x80000000u;   // gpos flag: carry slot, not an output position
+constexpr uint32_t kNoBucket = 0xFFFFu;      // past the end of a ragged tile
+
+template <int PAY>
+__host__ __device__ constexpr uint32_t wc_carry() {
+    return 32u / (uint32_t)sizeof(typename PayT<PAY>::T) - 1u;
+}
+
+template <int PAY>
+size_t wc_smem(uint32_t P) {
+    using T = typename PayT<PAY>::T;
+    return align256((size_t)P * sizeof(uint4)) + align256((size_t)P * sizeof(uint32_t)) +
+           align256((size_t)P * wc_carry<PAY>() * sizeof(T)) + TILE * sizeof(T) + TILE * sizeof(uint32_t);
+}
+
+template <int PAY>
+__global__ void __launch_bounds__(PT, 2) k_part_scatter_wc(
+    const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
+    uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
+    typename PayT<PAY>::T *__restrict__ out) {
+    using T = typename PayT<PAY>::T;
+    constexpr uint32_t CARRY = wc_carry<PAY>();
+    constexpr uint32_t SECT = CARRY + 1;   // tuples per 32-byte sector
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t P = sp.P();
+    // per bucket: x = the tile run's start in stage, y = tuples carried in,
+    // z = tuples of the run to write (W), w = global position of the run
+    uint4 *bs = (uint4 *)smem;
+    uint32_t *cnt = (uint32_t *)(smem + align256((size_t)P * sizeof(uint4)));
+    T *carry = (T *)((unsigned char *)cnt + align256((size_t)P * sizeof(uint32_t)));
+    T *stage = (T *)((unsigned char *)carry + align256((size_t)P * CARRY * sizeof(T)));
+    uint32_t *gpos = (uint32_t *)(stage + TILE);
+    __shared__ uint32_t scan_scratch[33];
+
+    const uint32_t G = gridDim.x;
+    for (uint32_t b = threadIdx.x; b < P; b += PT) {
+        bs[b] = make_uint4(0u, 0u, 0u, scanned[(size_t)b * G + blockIdx.x]);
+        cnt[b] = 0;
+    }
+    const Chunk c = cta_chunk(n, tiles_per_cta);
+    const bool vec = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
+    const uint32_t per = (P + PT - 1) / PT;
+    const uint64_t pol = l2_evict_first();
+    // thread t holds tuples 4t + {0..3} and TILE/2 + 4t + {0..3} of a tile
+    int32_t xs[IPT], ys[IPT];
+    auto load = [&](uint32_t t0) {
+        const uint32_t tn = min((uint32_t)TILE, c.end - t0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t li = (uint32_t)h * (TILE / 2) + threadIdx.x * 4;
+            if (vec && li + 3 < tn) {
+                const int4 a = ld_stream((const int4 *)(x + t0 + li), pol);
+                const int4 b = ld_stream((const int4 *)(y + t0 + li), pol);
+                xs[4 * h] = a.x; xs[4 * h + 1] = a.y; xs[4 * h + 2] = a.z; xs[4 * h + 3] = a.w;
+                ys[4 * h] = b.x; ys[4 * h + 1] = b.y; ys[4 * h + 2] = b.z; ys[4 * h + 3] = b.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t l = li + k;
+                    xs[4 * h + k] = l < tn ? __ldg(x + t0 + l) : 0;
+                    ys[4 * h + k] = l < tn ? __ldg(y + t0 + l) : 0;
+                }
+            }
+        }
+    };
+    if (c.begin < c.end) load(c.begin);
+    __syncthreads();
+
+    for (uint32_t t0 = c.begin; t0 < c.end; t0 += TILE) {
+        const uint32_t tn = min((uint32_t)TILE, c.end - t0);
+        const bool last = t0 + TILE >= c.end;
+        // 1. bucket and rank of every tuple, packed (bucket << 16 | rank);
+        //    a thread's runs of equal buckets among its 4 consecutive tuples
+        //    take one atomic each
+        uint32_t br[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t l = (uint32_t)(j >> 2) * (TILE / 2) + threadIdx.x * 4 + (j & 3);
+            uint32_t b = kNoBucket;
+            if (l < tn) {
+                if (sp.dom && (uint32_t)xs[j] >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xs[j]);
+                b = bucket_tuple(xs[j], ys[j], sp);
+            }
+            const bool cont = (j & 3) && b == (br[j - 1 < 0 ? 0 : j - 1] >> 16);
+            br[j] = (b << 16) | (cont ? (br[j - 1 < 0 ? 0 : j - 1] & 0xFFFFu) + 1u : 0u);   // place in its run
+        }
+        {
+            uint32_t base = 0;   // of the run being walked back from its end
+#pragma unroll
+            for (int j = IPT - 1; j >= 0; --j) {
+                const uint32_t b = br[j] >> 16;
+                const bool run_end = (j & 3) == 3 || (br[j + 1 < IPT ? j + 1 : j] >> 16) != b;
+                if (run_end && b != kNoBucket) base = atomicAdd(&cnt[b], (br[j] & 0xFFFFu) + 1u);
+                br[j] += base;
+            }
+        }
+        __syncthreads();
+        // 2. the tile's counts scanned into run starts; W = whole sectors of
+        //    carried + new (all of it in the CTA's last tile)
+        {
+            const uint32_t b0 = threadIdx.x * per;
+            uint32_t sum = 0;
+            for (uint32_t k = 0; k < per; ++k)
+                if (b0 + k < P) sum += cnt[b0 + k];
+            uint32_t base = block_excl_scan_u32(sum, scan_scratch, nullptr);
+            for (uint32_t k = 0; k < per; ++k) {
+                const uint32_t b = b0 + k;
+                if (b >= P) break;
+                uint4 v = bs[b];
+                const uint32_t L = v.y + cnt[b];
+                const uint32_t aligned = (v.w + L) & ~(SECT - 1u);
+                v.x = base;
+                v.z = last ? L : (aligned > v.w ? aligned - v.w : 0u);
+                bs[b] = v;
+                base += cnt[b];
+            }
+        }
+        __syncthreads();
+        // 3. stage the tile by bucket with each tuple's destination; write
+        //    the carried tuples of the runs that complete their sector
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t b = br[j] >> 16, rk = br[j] & 0xFFFFu;
+            if (b != kNoBucket) {
+                const uint4 v = bs[b];
+                const uint32_t p = v.x + rk, r = v.y + rk;
+                stage[p] = make_pay<PAY>(xs[j], ys[j]);
+                gpos[p] = r < v.z ? v.w + r : (kToCarry | (b * CARRY + (r - v.z)));
+            }
+        }
+        for (uint32_t b = threadIdx.x; b < P; b += PT) {
+            const uint4 v = bs[b];
+            if (v.z)
+                for (uint32_t q = 0; q < v.y; ++q) st_stream(out + v.w + q, carry[b * CARRY + q], pol);
+        }
+        if (!last) load(t0 + TILE);   // the next tile's loads fly during the write-out
+        __syncthreads();
+        // 4. write the tile: whole sectors out, the rest into the carry slots
+        for (uint32_t e = threadIdx.x; e < tn; e += PT) {
+            const uint32_t g = gpos[e];
+            const T v = stage[e];
+            if (g & kToCarry) carry[g & ~kToCarry] = v;
+            else st_stream(out + g, v, pol);
+        }
+        __syncthreads();
+        // 5. the next run starts where this one's writes ended
+        for (uint32_t b = threadIdx.x; b < P; b += PT) {
+            uint4 v = bs[b];
+            const uint32_t L = v.y + cnt[b];
+            v.w += v.z;
+            v.y = L - v.z;
+            bs[b] = v;
+            cnt[b] = 0;
+        }
+        __syncthreads();
+    }
+}
+
 // K3 (P > 4096): direct scatter through shared-memory cursors.
 template <int PAY>
 __global__ void __launch_bounds__(PT) k_part_scatter_direct(
@@ -362,7 +555,15 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
                            Geometry g, const uint32_t *scanned, void *out, cudaStream_t st) {
     using T = typename PayT<PAY>::T;
     const uint32_t P = sp.P();
-    if (P <= kStagedMaxP) {
+    if (P <= kWcMaxP) {
+        const size_t smem = wc_smem<PAY>(P);
+        auto kern = k_part_scatter_wc<PAY>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        ProfScope ps_("part_scatter", st);
+        kern<<<g.G, PT, smem, st>>>(x, y, n, sp, g.tiles_per_cta, scanned, (T *)out);
+    } else if (P <= kStagedMaxP) {
         size_t smem = align256(3 * P * sizeof(uint32_t)) + TILE * sizeof(T) + TILE * sizeof(uint32_t) +
                       2 * TILE * sizeof(int32_t);
         auto kern = k_part_scatter_staged<PAY>;
@@ -406,14 +607,19 @@ cudaError_t part_run(const int32_t *x, const int32_t *y, int64_t n64, const Part
     int occ = 1;
     {
         const bool staged = P <= kStagedMaxP;
-        size_t ssz = payload == PAY_PAIR ? sizeof(uint2) : sizeof(uint32_t);
+        const bool pair = payload == PAY_PAIR;
+        size_t ssz = pair ? sizeof(uint2) : sizeof(uint32_t);
         size_t smem = staged ? align256(3 * P * sizeof(uint32_t)) + TILE * ssz + TILE * sizeof(uint32_t) +
                                    2 * TILE * sizeof(int32_t)
                              : P * sizeof(uint32_t);
-        const void *kern = staged ? (payload == PAY_PAIR ? (const void *)k_part_scatter_staged<PAY_PAIR>
-                                                         : (const void *)k_part_scatter_staged<PAY_X>)
-                                  : (payload == PAY_PAIR ? (const void *)k_part_scatter_direct<PAY_PAIR>
-                                                         : (const void *)k_part_scatter_direct<PAY_X>);
+        const void *kern = staged ? (pair ? (const void *)k_part_scatter_staged<PAY_PAIR>
+                                          : (const void *)k_part_scatter_staged<PAY_X>)
+                                  : (pair ? (const void *)k_part_scatter_direct<PAY_PAIR>
+                                          : (const void *)k_part_scatter_direct<PAY_X>);
+        if (P <= kWcMaxP && !z) {
+            smem = pair ? wc_smem<PAY_PAIR>(P) : wc_smem<PAY_X>(P);
+            kern = pair ? (const void *)k_part_scatter_wc<PAY_PAIR> : (const void *)k_part_scatter_wc<PAY_X>;
+        }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PT, smem) != cudaSuccess || occ < 1)
             occ = 1;

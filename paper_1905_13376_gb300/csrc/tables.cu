@@ -388,23 +388,29 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
     for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) r[j] = 0;
     __syncthreads();
     const bool vec = ((uintptr_t)keys & 15) == 0;
+    const uint64_t pol = l2_evict_first();
     const uint32_t stride = gridDim.x * BT * 4;
     for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * 4; i < n; i += stride) {
         int32_t v[4];
         if (vec && i + 3 < n) {
-            int4 q = __ldg((const int4 *)(keys + i));
+            int4 q = ld_stream((const int4 *)(keys + i), pol);
             v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
         }
+        // a register only grows, so a key equal to its predecessor and a rank
+        // the register already holds change nothing (runs of equal keys are
+        // common: edge lists come sorted by source)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (i + k >= n) break;
+            if (k > 0 && v[k] == v[k - 1]) continue;
             const uint32_t h = mix32((uint32_t)v[k] ^ seed);
             const uint32_t w = h << HLL_BITS;
             const uint32_t rank = (w == 0) ? (33u - HLL_BITS) : (uint32_t)__clz(w) + 1u;
-            atomicMax(&r[h >> (32 - HLL_BITS)], rank);
+            unsigned int *reg = &r[h >> (32 - HLL_BITS)];
+            if (*(volatile unsigned int *)reg < rank) atomicMax(reg, rank);
         }
     }
     __syncthreads();
@@ -468,6 +474,7 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
                                                        const uint32_t *__restrict__ meta, DevStatus *st) {
     const uint32_t mask = meta[0];
     const bool vec = ((uintptr_t)keys & 15) == 0;
+    const uint64_t pol = l2_evict_first();
     constexpr uint32_t K = 8;
     const uint32_t stride = gridDim.x * BT * K;
     for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * K; i < n; i += stride) {
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
         if (vec && i + K - 1 < n) {
 #pragma unroll
             for (uint32_t q = 0; q < K / 4; ++q) {
-                int4 a = __ldg((const int4 *)(keys + i) + q);
+                int4 a = ld_stream((const int4 *)(keys + i) + q, pol);
                 v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
             }
         } else {
