@@ -59,7 +59,7 @@ typedef enum {
     MWJ_MATERIALIZE = 2        /* the joined tuples into rows, plus *n_rows and *total */
 } mwj_mode;
 
-typedef enum { MWJ_LINEAR = 0, MWJ_CYCLIC = 1 } mwj_kind;
+typedef enum { MWJ_LINEAR = 0, MWJ_CYCLIC = 1, MWJ_STAR = 4 } mwj_kind;
 
 /* One relation: n tuples (x[i], y[i]).  Linear: R = (a,b), S = (b,c),
  * T = (c,d).  Cyclic: R = (a,b), S = (b,c), T = (c,a).  Device, borrowed,
@@ -113,8 +113,9 @@ typedef struct mwj_ctx mwj_ctx;
 mwj_status mwj_create(mwj_ctx **ctx, const mwj_config *cfg);
 mwj_status mwj_destroy(mwj_ctx *ctx);
 
-/* Bytes of device workspace a call needs.  kind: MWJ_LINEAR / MWJ_CYCLIC for
- * mwj_join3_*, or 2 + kind for mwj_cascade_join.  For the cascade the size
+/* Bytes of device workspace a call needs.  kind: MWJ_LINEAR / MWJ_CYCLIC /
+ * MWJ_STAR for mwj_join3_*, or 2 + kind (linear or cyclic) for
+ * mwj_cascade_join.  For the cascade the size
  * includes room for 2^24 rows of the intermediate relation I; the cascade
  * uses every byte it is given beyond its fixed part as room for I, at 12
  * bytes per row (linear), 20 (cyclic counts) or 24 (cyclic rows), and works
@@ -139,6 +140,19 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
 mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
                             const mwj_shares *shares, const mwj_out *out,
                             void *workspace, size_t ws_bytes, void *stream);
+
+/* Star 3-way join R(A,B) S(B,C) T(C,D) (Section 6, "linear star 3-way
+ * join"): the same query and outputs as mwj_join3_linear, planned for small
+ * dimension relations R and T and a large fact relation S.  R is grouped by
+ * h(B) and T by g(C) into bucket tables that stay on chip (L2 and L1); S is
+ * read once, unpartitioned, each tuple looked up in both tables (twice for
+ * MATERIALIZE: a counting pass, then the rows).  shares: s[0] = h(B) buckets
+ * of R, s[1] = g(C) buckets of T (0 or shares == NULL: about 2048 tuples per
+ * bucket); s[2] is ignored.  GROUP BY A checks the domain of A while it adds
+ * R's groups (MWJ_ERR_DOMAIN from mwj_stream_status).
+ * workspace: device, >= mwj_workspace_size(ctx, MWJ_STAR, ...). */
+mwj_status mwj_join3_star(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, const mwj_shares *shares,
+                          const mwj_out *out, void *workspace, size_t ws_bytes, void *stream);
 
 /* Cascade of binary hash joins (Section 6.3): I(A,B,C) = R join S is
  * materialised in the workspace (in chunks when it does not fit), then
@@ -203,7 +217,8 @@ mwj_status mwj_batch_launch(mwj_batch *batch, int64_t *counts, void *workspace, 
 mwj_status mwj_batch_destroy(mwj_batch *batch);
 
 /* The shares the planner would choose for these relations (host result in
- * *shares).  kind = MWJ_LINEAR or MWJ_CYCLIC.  Synchronises `stream`. */
+ * *shares).  kind = MWJ_LINEAR, MWJ_CYCLIC or MWJ_STAR.  Synchronises
+ * `stream`. */
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
                            mwj_mode mode, mwj_shares *shares, void *stream);
 

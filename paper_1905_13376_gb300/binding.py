@@ -31,6 +31,7 @@ MWJ_MATERIALIZE = 2
 
 MWJ_LINEAR = 0
 MWJ_CYCLIC = 1
+MWJ_STAR = 4
 
 MODES = {"count": MWJ_COUNT, "group_by_a": MWJ_COUNT_GROUP_BY_A, "rows": MWJ_MATERIALIZE}
 
@@ -82,6 +83,8 @@ _SIGS = {
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_join3_cyclic": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_join3_star": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
+                                      ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
@@ -273,10 +276,11 @@ class Context:
         if isinstance(mode, str):
             mode = MODES[mode]
         o, res = self._outputs(mode, a_domain, capacity, arity)
-        nb = self.workspace_size(kind_ws, R, S, T, shares if kind_ws < 2 else None, mode)
+        with_shares = kind_ws in (MWJ_LINEAR, MWJ_CYCLIC, MWJ_STAR)
+        nb = self.workspace_size(kind_ws, R, S, T, shares if with_shares else None, mode)
         ws = self.workspace(nb)
         args = (self.h,) + tuple(extra) + (_rel(R), _rel(S), _rel(T))
-        if kind_ws < 2:
+        if with_shares:
             args = args + (_shares(shares),)
         st = fn(*args, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                 self._stream(stream))
@@ -291,6 +295,14 @@ class Context:
     def join3_linear(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
                      stream=None, sync=True):
         return self._run(self.lib.mwj_join3_linear, MWJ_LINEAR, R, S, T, mode, shares, a_domain,
+                         capacity, 4, stream, sync)
+
+    def join3_star(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
+                   stream=None, sync=True):
+        """Star 3-way join: small R(A,B) and T(C,D) held on chip, S(B,C)
+        streamed once.  shares = (h(B) buckets of R, g(C) buckets of T), 0 or
+        None for the default."""
+        return self._run(self.lib.mwj_join3_star, MWJ_STAR, R, S, T, mode, shares, a_domain,
                          capacity, 4, stream, sync)
 
     def join3_cyclic(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,

@@ -300,6 +300,7 @@ mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_
     if (kind == MWJ_CYCLIC) return cyc_workspace(ctx, R, S, T, shares, mode, bytes);
     if (kind == 2 + MWJ_LINEAR || kind == 2 + MWJ_CYCLIC)
         return cascade_workspace(ctx, kind - 2, R, S, T, mode, bytes);
+    if (kind == MWJ_STAR) return star_workspace(ctx, R, S, T, shares, mode, bytes);
     return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind %d", kind);
 }
 
@@ -402,6 +403,7 @@ mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel
     if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
     if (kind == MWJ_LINEAR) return plan_linear_default(ctx, R, S, T, shares);
     if (kind == MWJ_CYCLIC) return plan_cyclic_default(ctx, R, S, T, shares);
+    if (kind == MWJ_STAR) return plan_star_default(R, T, shares);
     return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind");
 }
 

@@ -34,6 +34,9 @@ mwj_status plan_cyclic_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S,
                                mwj_shares *sh);
 mwj_status cyc_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
                          const mwj_shares *shares, mwj_mode mode, size_t *bytes);
+mwj_status star_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                          const mwj_shares *shares, mwj_mode mode, size_t *bytes);
+mwj_status plan_star_default(const mwj_rel &R, const mwj_rel &T, mwj_shares *sh);
 mwj_status cascade_workspace(mwj_ctx *ctx, int kind, const mwj_rel &R, const mwj_rel &S,
                              const mwj_rel &T, mwj_mode mode, size_t *bytes);
 

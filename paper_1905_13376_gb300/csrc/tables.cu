@@ -383,8 +383,10 @@ constexpr uint32_t HLL_M = 1u << HLL_BITS;
 // of the remaining bits.  mix32 is a bijection of 32-bit keys, so distinct
 // keys have distinct hashes.
 __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, uint32_t n,
-                                            uint32_t seed, unsigned int *__restrict__ regs) {
+                                            uint32_t seed, unsigned int *__restrict__ regs,
+                                            unsigned int *__restrict__ done) {
     __shared__ unsigned int r[HLL_M];
+    if (done && blockIdx.x == 0 && threadIdx.x == 0) *done = 0;   // for k_hll_merge_size
     for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) r[j] = 0;
     __syncthreads();
     const bool vec = ((uintptr_t)keys & 15) == 0;
@@ -429,42 +431,67 @@ __global__ void k_hll_merge(unsigned int *__restrict__ regs, uint32_t ctas) {
     regs[j] = m;
 }
 
-// estimate -> table of 2^k >= factor x estimate slots (at most `reserve`)
-__global__ void k_hll_size(const unsigned int *__restrict__ regs, uint64_t reserve, double factor,
-                           uint32_t *__restrict__ meta) {
-    __shared__ double part[32];
-    __shared__ unsigned int zeros[32];
-    double s = 0.0;
-    unsigned int z = 0;
-    for (uint32_t j = threadIdx.x; j < HLL_M; j += blockDim.x) {
-        s += ldexp(1.0, -(int)regs[j]);
-        z += (regs[j] == 0);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        z += __shfl_xor_sync(0xffffffffu, z, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        part[threadIdx.x >> 5] = s;
-        zeros[threadIdx.x >> 5] = z;
+constexpr uint32_t HLL_MB = 32;                  // registers merged per CTA
+constexpr uint32_t HLL_MCTAS = HLL_M / HLL_MB;   // merge CTAs
+// after the per-CTA registers: per merge CTA its part of the estimator's sum
+// (double) and of the empty-register count, then the finish counter
+constexpr size_t HLL_TAIL = 2 * HLL_MCTAS + HLL_MCTAS + 8;
+
+// Merge the per-CTA registers (maximum over `rows` rows) into row 0 and size
+// the table: CTA b merges registers [32 b, 32 b + 32) and leaves its part of
+// sum(2^-reg) and of the zero count; the last CTA to finish adds the parts
+// in a fixed order (so the estimate does not depend on the finishing order)
+// and writes meta: table of 2^k >= factor x estimate slots (at most
+// `reserve`).
+__global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict__ regs, uint32_t rows,
+                                                        unsigned int *__restrict__ tail, uint64_t reserve,
+                                                        double factor, uint32_t *__restrict__ meta) {
+    __shared__ unsigned int m[8][HLL_MB];
+    __shared__ bool last;
+    double *part_s = (double *)tail;
+    unsigned int *part_z = tail + 2 * HLL_MCTAS;
+    unsigned int *done = part_z + HLL_MCTAS;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t j = blockIdx.x * HLL_MB + lane;
+    unsigned int mx = 0;
+    for (uint32_t r = w; r < rows; r += 8) mx = max(mx, regs[(size_t)r * HLL_M + j]);
+    m[w][lane] = mx;
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 1; q < 8; ++q) mx = max(mx, m[q][lane]);
+        regs[j] = mx;
+        double sum = 1.0 / (double)(1ull << mx);   // exact: ranks are at most 33 - HLL_BITS
+        unsigned int z = (mx == 0);
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) {
+            part_s[blockIdx.x] = sum;
+            part_z[blockIdx.x] = z;
+            __threadfence();
+            last = atomicAdd(done, 1u) == gridDim.x - 1;
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double S = 0.0;
-        unsigned int Z = 0;
-        for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-            S += part[w];
-            Z += zeros[w];
-        }
-        const double m = (double)HLL_M;
-        double E = (0.7213 / (1.0 + 1.079 / m)) * m * m / S;
-        if (E <= 2.5 * m && Z > 0) E = m * log(m / (double)Z);   // small-range correction
-        uint64_t cap = 16;
-        while ((double)cap < factor * E && cap < reserve) cap <<= 1;
-        if (cap > reserve) cap = reserve;
-        meta[0] = (uint32_t)(cap - 1);
-        meta[1] = (uint32_t)E;
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double S = 0.0;
+    unsigned int Z = 0;
+    for (uint32_t b = 0; b < gridDim.x; ++b) {
+        S += __ldcg(part_s + b);
+        Z += __ldcg(part_z + b);
     }
+    const double mm = (double)HLL_M;
+    double E = (0.7213 / (1.0 + 1.079 / mm)) * mm * mm / S;
+    if (E <= 2.5 * mm && Z > 0) E = mm * log(mm / (double)Z);   // small-range correction
+    uint64_t cap = 16;
+    while ((double)cap < factor * E && cap < reserve) cap <<= 1;
+    if (cap > reserve) cap = reserve;
+    meta[0] = (uint32_t)(cap - 1);
+    meta[1] = (uint32_t)E;
+    *done = 0;
 }
 
 // insert T's C column; each thread merges runs of equal keys among 8
@@ -514,21 +541,21 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
     cudaError_t e;
     const uint32_t nn = (uint32_t)n;
     const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
+    unsigned int *tail = hll_regs + (size_t)ctas * HLL_M;
+    unsigned int *done = tail + 3 * HLL_MCTAS;
+    uint32_t rows = ctas;
     if (nn > 0) {
-        {
-            ProfScope ps_("t_hll", st);
-            k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs);
-        }
-        {
-            ProfScope ps_("t_hll_merge", st);
-            k_hll_merge<<<(HLL_M + 255) / 256, 256, 0, st>>>(hll_regs, ctas);
-        }
-    } else if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) {
-        return e;
+        ProfScope ps_("t_hll", st);
+        k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs, done);
+    } else {
+        rows = 1;
+        if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(done, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     }
     {
         ProfScope ps_("t_size", st);
-        k_hll_size<<<1, 1024, 0, st>>>(hll_regs, reserve_slots, kSingleTableFactor, meta);
+        k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor,
+                                                   meta);
     }
     {
         ProfScope ps_("t_clear", st);
@@ -552,7 +579,7 @@ cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int
         const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
         {
             ProfScope ps_("sketch_hll", st);
-            k_hll<<<ctas, BT, 0, st>>>(keys, (uint32_t)n, seed, regs);
+            k_hll<<<ctas, BT, 0, st>>>(keys, (uint32_t)n, seed, regs, nullptr);
         }
         ProfScope ps_("sketch_hll_merge", st);
         k_hll_merge<<<(HLL_M + 255) / 256, 256, 0, st>>>(regs, ctas);
@@ -562,6 +589,6 @@ cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int
     return cudaGetLastError();
 }
 
-size_t hll_scratch_registers(int num_sms) { return (size_t)num_sms * HLL_CTAS_PER_SM * HLL_M; }
+size_t hll_scratch_registers(int num_sms) { return (size_t)num_sms * HLL_CTAS_PER_SM * HLL_M + HLL_TAIL; }
 
 }  // namespace mwj

@@ -63,7 +63,8 @@ cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32
 
 // One table without partitioning T: a HyperLogLog pass over the keys sizes
 // the table (2^k >= 4 x the estimate, at most reserve_slots), then the keys
-// are inserted directly.  hll_regs: hll_scratch_registers(num_sms) u32; meta: 2 u32.
+// are inserted directly.  hll_regs: hll_scratch_registers(num_sms) u32 (per-CTA
+// registers, then the sizing step's partial sums); meta: 2 u32.
 cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
                                 DevStatus *status, int num_sms, cudaStream_t st);

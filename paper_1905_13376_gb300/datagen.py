@@ -24,6 +24,13 @@ Workload recipes (sizes as in the headline configurations):
 * ``chung_lu_undirected``: the same weight law on 2^22 vertices with mean
   undirected degree 32; both endpoints are drawn from the same weights,
   self loops and duplicates are dropped and every edge is oriented a < b.
+* ``star_schema``: the star join of Section 6 (a large fact relation with
+  two small dimension relations, TPC-H's lineitem with orders and supplier):
+  R(A,B) and T(C,D) of 2^20 tuples each whose join keys B and C are unique
+  (a random permutation of [0, 2^20)), A and D uniform attributes in
+  [0, 2^16); the fact relation S(B,C) of 2^26 tuples holds foreign keys
+  drawn uniformly (or Zipf(1.0) through a bijection) from the dimension
+  keys, sorted by B like lineitem is by orderkey.
 * ``batched_queries``: many small independent joins with log-uniform sizes
   and key domains, keys uniform or Zipf(1.0) (P(k) proportional to
   1/(k+1), then mapped through a bijection of the domain).
@@ -192,6 +199,24 @@ def _keys(g, n: int, domain: int, zipf: bool, s: float = 1.0) -> np.ndarray:
             break
     off = int(g.integers(0, domain))
     return ((k * mult + off) % domain).astype(np.int32)
+
+
+def star_schema(n_fact: int = 1 << 26, n_dim: int = 1 << 20, attr_domain: int = 1 << 16,
+                zipf: bool = False, sorted_fact: bool = True, seed: int = SEED_BASE + 5):
+    """(R, S, T) of a star join: dimensions R(A,B), T(C,D) with unique keys,
+    fact S(B,C) of foreign keys into them (every S tuple joins exactly one R
+    and one T tuple)."""
+    g = _rng(seed)
+    rb = g.permutation(n_dim).astype(np.int32)
+    ra = g.integers(0, attr_domain, size=n_dim, dtype=np.int64).astype(np.int32)
+    tc = g.permutation(n_dim).astype(np.int32)
+    td = g.integers(0, attr_domain, size=n_dim, dtype=np.int64).astype(np.int32)
+    sb = _keys(g, n_fact, n_dim, zipf)
+    sc = _keys(g, n_fact, n_dim, zipf)
+    if sorted_fact:
+        o = np.argsort(sb, kind="stable")
+        sb, sc = sb[o], sc[o]
+    return (ra, rb), (np.ascontiguousarray(sb), np.ascontiguousarray(sc)), (tc, td)
 
 
 def random_query(g, kind: str, size_lo: int = 1 << 8, size_hi: int = 1 << 18,
