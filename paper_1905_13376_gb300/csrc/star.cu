@@ -27,9 +27,9 @@
 namespace mwj {
 namespace {
 
-constexpr int ST = 384;                 // threads per CTA (two CTAs per SM at up to 85 registers)
+constexpr int ST = 256;                 // threads per CTA (four CTAs per SM at up to 64 registers)
 constexpr int SB = 4;                   // S tuples per thread per batch
-constexpr int kStarCtasPerSm = 2;
+constexpr int kStarCtasPerSm = 4;
 
 // CTA c of G streams S tuples [c * chunk, (c + 1) * chunk), chunk a multiple
 // of 4 * SB so that every chunk starts 16-byte aligned.
