@@ -258,6 +258,8 @@ def run_ours(args, rank, world, local_rank):
                 "intermediate_rows": nI, "intermediate_bytes": 12 * nI, "steps": csteps,
                 "multiway_speedup": cms / ms, "exact_match": True}
 
+    star = None if args.no_star else run_star(ctx, stream, args, peaks())
+
     # max over ranks
     if world > 1:
         t = torch.tensor([ms, e2e_ms], device=dev)
@@ -267,10 +269,10 @@ def run_ours(args, rank, world, local_rank):
     tuples = 3 * n
     value = tuples * world / (ms * 1e-3)
     peak, peak_kind = peaks()
-    # T's single table: 2^k >= 2 x (distinct C values) slots of 8 bytes
+    # T's single table: 2^k >= 4 x (estimated distinct C values) slots of 8 bytes
     dc = int(np.count_nonzero(np.bincount(F[0], minlength=a_domain)))
     tslots = 16
-    while tslots < 2 * dc:
+    while tslots < 4 * dc:
         tslots *= 2
     # dominant kernel and its roofline
     per_step = {k: v[0] / args.steps for k, v in phases.items()}
@@ -301,9 +303,70 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "kernels": kernels,
         "e2e": {"value": tuples * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
-        "gpu_launches": launches, "clocks": clocks, "cascade": casc,
+        "gpu_launches": launches, "clocks": clocks, "cascade": casc, "star": star,
     }
     return out, F
+
+
+def run_star(ctx, stream, args, pk):
+    """The star 3-way join (fact relation streamed once past two dimension
+    tables) against the cascade of binary joins on the same inputs."""
+    import numpy as np
+    import torch
+    from paper_1905_13376_gb300 import binding, datagen
+
+    R, S, T = datagen.star_schema()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = lambda rel: tuple(torch.from_numpy(c).to(dev) for c in rel)
+    dR, dS, dT = d(R), d(S), d(T)
+    adom = 1 << 16
+    nS, nR, nT = len(S[0]), len(R[0]), len(T[0])
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    r = ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom)
+    # closed form: every fact tuple joins one tuple of each dimension
+    inv = np.empty(nR, dtype=np.int64)
+    inv[R[1]] = np.arange(nR)
+    want = np.bincount(R[0][inv[S[0]]], minlength=adom)
+    exact = int(r["total"].item()) == nS and np.array_equal(r["counts"].cpu().numpy(), want)
+    ms = timed(lambda: ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom, sync=False), args.steps)
+    ctx.set_profiling(True)
+    ctx.reset_phase_times()
+    for _ in range(args.steps):
+        ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom, sync=False)
+    torch.cuda.synchronize()
+    ph = ctx.phase_times()
+    ctx.set_profiling(False)
+    probe_ms = ph.get("star_probe_groupby", (float("nan"), 0))[0] / args.steps
+    # the probe reads S once (8 B per tuple) and both degree tables once
+    slots = lambda n: 1 << max(4, int(np.ceil(np.log2(4 * n))))
+    pbytes = 8 * nS + 8 * (slots(nR) + slots(nT))
+    ach = pbytes / (probe_ms * 1e-3) / 1e9
+    rc = ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom)
+    exact = exact and torch.equal(rc["counts"], r["counts"])
+    cms = timed(lambda: ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom,
+                                         sync=False), max(3, args.steps // 4))
+    return {"workload": f"star join: fact S(B,C) {nS} tuples (foreign keys, sorted by B), "
+                        f"dimensions R(A,B), T(C,D) {nR} tuples each (unique keys), "
+                        f"COUNT(*) GROUP BY A over 2^16 groups",
+            "value": (nS + nR + nT) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "exact_match": bool(exact),
+            "probe": {"kernel": "star_probe_groupby", "ms_per_step": round(probe_ms, 4),
+                      "algorithmic_bytes": pbytes, "achieved": round(ach, 1), "peak": pk[0],
+                      "unit": "GB/s", "frac": round(ach / pk[0], 4), "peak_kind": pk[1]},
+            "cascade_ms_per_step": cms, "multiway_speedup": cms / ms}
 
 
 def cpu_baseline(F, a_domain, budget_s=30.0):
@@ -353,6 +416,8 @@ def main():
                     help="I J [log2 table slots]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-star", action="store_true",
+                    help="skip the star-join arm (fact relation 2^26 tuples)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
