@@ -7,7 +7,9 @@ code with that path.
 
 ``linear`` and ``cyclic`` evaluate the plain relational definitions of
 Section 3 (linear R(A,B) S(B,C) T(C,D); cyclic R(A,B) S(B,C) T(C,A)) under
-bag semantics with a single-threaded C hash join (``oracle.c``).  Counts are
+bag semantics with a single-threaded C hash join (``oracle.c``);
+``linear4`` the chain one relation longer, R(A,B) S(B,C) T(C,D) U(D,E)
+(Section 7's additional hash levels), for COUNT and GROUP BY A.  Counts are
 unsigned 64-bit with wraparound and are returned as ``int64`` views of the
 same bits, the width the CUDA path reports.
 """
@@ -60,6 +62,9 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = sig
                 f.restype = ctypes.c_int
+            lib.oracle_linear4.argtypes = [P, P, I64, P, P, I64, P, P, I64, P, P, I64, ctypes.c_int,
+                                           ctypes.c_int32, P, P]
+            lib.oracle_linear4.restype = ctypes.c_int
             lib.oracle_binary_count.argtypes = [P, I64, P, I64, P]
             lib.oracle_binary_count.restype = ctypes.c_int
             _lib = lib
@@ -119,6 +124,27 @@ def cyclic(R, S, T, mode=COUNT, a_domain=None, capacity=None, check=True):
     out = _run(_load().oracle_cyclic, R, S, T, mode, a_domain, capacity, 3)
     if check and out["rc"] != 0:
         raise OracleError(f"oracle_cyclic returned {out['rc']}")
+    return out
+
+
+def linear4(R, S, T, U, mode=COUNT, a_domain=None, check=True):
+    """R(A,B) S(B,C) T(C,D) U(D,E): COUNT or COUNT GROUP BY A."""
+    cols = [_col(c) for rel in (R, S, T, U) for c in rel]
+    for k in range(0, 8, 2):
+        if len(cols[k][0]) != len(cols[k + 1][0]):
+            raise ValueError("column lengths differ")
+    total = np.zeros(1, dtype=np.uint64)
+    cnt = np.zeros(int(a_domain), dtype=np.uint64) if mode == GROUP_BY_A else None
+    args = []
+    for k in range(0, 8, 2):
+        args += [cols[k][1], cols[k + 1][1], len(cols[k][0])]
+    rc = _load().oracle_linear4(*args, int(mode), int(a_domain or 0), total.ctypes.data,
+                                cnt.ctypes.data if cnt is not None else None)
+    if check and rc != 0:
+        raise OracleError(f"oracle_linear4 returned {rc}")
+    out = {"rc": rc, "total": int(total.view(np.int64)[0])}
+    if cnt is not None:
+        out["counts"] = cnt.view(np.int64)
     return out
 
 

@@ -200,6 +200,58 @@ int oracle_linear(const int32_t *Ra, const int32_t *Rb, int64_t nR,
     return 0;
 }
 
+/* ---------- linear 4-way: R(A,B) S(B,C) T(C,D) U(D,E) -------------------- */
+/*
+ * The chain one relation longer (Section 7's "additional levels of
+ * hashing"):  Out4 = { (a,b,c,d,e) : (a,b) in R, (b,c) in S, (c,d) in T,
+ * (d,e) in U }.  COUNT(*) and COUNT(*) GROUP BY A; for every S tuple (b,c)
+ * the matching T tuples (c,d) are walked and each contributes deg_U(d), the
+ * number of its U tuples.
+ */
+int oracle_linear4(const int32_t *Ra, const int32_t *Rb, int64_t nR,
+                   const int32_t *Sb, const int32_t *Sc, int64_t nS,
+                   const int32_t *Tc, const int32_t *Td, int64_t nT,
+                   const int32_t *Ud, const int32_t *Ue, int64_t nU,
+                   int mode, int32_t a_domain, uint64_t *total, uint64_t *cnt) {
+    if (nR < 0 || nS < 0 || nT < 0 || nU < 0 || !total) return 1;
+    if (mode != O_COUNT && mode != O_GROUP_BY_A) return 1;
+    if (mode == O_GROUP_BY_A) {
+        if (a_domain <= 0 || !cnt) return 1;
+        int rc = check_domain(Ra, nR, a_domain);
+        if (rc) return rc;
+        memset(cnt, 0, (size_t)a_domain * sizeof(uint64_t));
+    }
+    ogroup RB, TC, UD;                 /* b -> [a],  c -> [d],  d -> [e] */
+    int rc = ogroup_build(&RB, Rb, Ra, nR);
+    if (rc) return rc;
+    rc = ogroup_build(&TC, Tc, Td, nT);
+    if (rc) { ogroup_free(&RB); return rc; }
+    rc = ogroup_build(&UD, Ud, Ue, nU);
+    if (rc) { ogroup_free(&RB); ogroup_free(&TC); return rc; }
+
+    uint64_t tot = 0;
+    for (int64_t s = 0; s < nS; ++s) {
+        int64_t i = omap_find(&RB.map, key32(Sb[s]));
+        if (i < 0) continue;
+        int64_t j = omap_find(&TC.map, key32(Sc[s]));
+        if (j < 0) continue;
+        uint64_t tail = 0;             /* (c,d,e) continuations of this (b,c) */
+        for (int64_t q = TC.start[j]; q < TC.start[j + 1]; ++q) {
+            int64_t u = omap_find(&UD.map, key32(TC.vals[q]));
+            if (u >= 0) tail += (uint64_t)(UD.start[u + 1] - UD.start[u]);
+        }
+        uint64_t degR = (uint64_t)(RB.start[i + 1] - RB.start[i]);
+        tot += degR * tail;
+        if (mode == O_GROUP_BY_A)
+            for (int64_t p = RB.start[i]; p < RB.start[i + 1]; ++p) cnt[RB.vals[p]] += tail;
+    }
+    *total = tot;
+    ogroup_free(&RB);
+    ogroup_free(&TC);
+    ogroup_free(&UD);
+    return 0;
+}
+
 /* ---------- cyclic: R(A,B) S(B,C) T(C,A) --------------------------------- */
 
 int oracle_cyclic(const int32_t *Ra, const int32_t *Rb, int64_t nR,
