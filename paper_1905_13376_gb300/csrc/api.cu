@@ -7,6 +7,7 @@
 #include "api_internal.h"
 #include "linear.h"
 #include "tables.h"
+#include "skew.h"
 
 using namespace mwj;
 
@@ -64,6 +65,7 @@ struct LinPlan {
     uint32_t I, J, JT;
     bool rows;
     bool single;   // T in one L2-resident table (S not split by C, count modes)
+    bool heavy;    // aggregates: heavy B keys split off into one extra bucket
 };
 
 // bucket count of T's tables: small buckets so that each is aggregated in
@@ -77,6 +79,7 @@ uint32_t t_buckets(int64_t nT, uint32_t J, bool single) {
 }
 
 struct LinLayout {
+    uint32_t *heavy; unsigned long long *hw;
     uint2 *Rp; uint32_t *offR;
     uint2 *Sp; uint32_t *offS;
     uint32_t *Tk; uint2 *Tp; uint32_t *offT;
@@ -89,10 +92,13 @@ struct LinLayout {
 
 size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S,
                   const mwj_rel &T, int num_sms, LinLayout &L) {
+    const uint32_t extra = p.heavy ? 1u : 0u;   // the heavy-key bucket
+    L.heavy = p.heavy ? A.take<uint32_t>(kHeavyTableWords) : nullptr;
+    L.hw = p.heavy ? A.take<unsigned long long>(kHeavySlots) : nullptr;
     L.Rp = A.take<uint2>(R.n + 2);
-    L.offR = A.take<uint32_t>(p.I + 1);
+    L.offR = A.take<uint32_t>(p.I + extra + 1);
     L.Sp = A.take<uint2>(S.n + 2);
-    L.offS = A.take<uint32_t>((size_t)p.I * p.J + 1);
+    L.offS = A.take<uint32_t>((size_t)p.I * p.J + extra + 1);
     if (p.single) {
         // T stays unpartitioned: one table sized from a HyperLogLog estimate
         L.Tk = nullptr;
@@ -129,8 +135,8 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
         L.rowcount = L.base = nullptr;
         L.sscratch = nullptr;
     }
-    size_t ps = part_scratch_bytes(R.n, p.I, num_sms);
-    size_t ps2 = part_scratch_bytes(S.n, p.I * p.J, num_sms);
+    size_t ps = part_scratch_bytes(R.n, p.I + extra, num_sms);
+    size_t ps2 = part_scratch_bytes(S.n, p.I * p.J + extra, num_sms);
     size_t ps3 = p.single ? 0 : part_scratch_bytes(T.n, p.JT, num_sms);
     if (ps2 > ps) ps = ps2;
     if (ps3 > ps) ps = ps3;
@@ -291,6 +297,7 @@ mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_
         if (s != MWJ_OK) return s;
         p.rows = (mode == MWJ_MATERIALIZE);
         p.single = (p.J == 1 && !p.rows);
+        p.heavy = !p.rows;
         p.JT = t_buckets(T.n, p.J, p.single);
         Arena A(nullptr, 0);
         LinLayout L;
@@ -320,6 +327,7 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     if (s != MWJ_OK) return s;
     p.rows = (out->mode == MWJ_MATERIALIZE);
     p.single = (p.J == 1 && !p.rows);
+    p.heavy = !p.rows;
     p.JT = t_buckets(T.n, p.J, p.single);
     Arena A(workspace, ws_bytes);
     LinLayout L;
@@ -344,13 +352,18 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
                      L.offT, L.pscratch, L.pscratch_bytes, ctx->dev.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "partition T");
     }
+    // heavy B keys (aggregates): named from samples of R's and S's B columns
+    if (p.heavy && (e = heavy_detect(R.y, R.n, S.x, S.n, p.I, L.heavy, L.hw, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "heavy keys");
     PartSpec ps{0, sd.B, p.I, p.J > 1 ? 1 : -1, sd.C, p.J};
     ps.st = ctx->status;
+    ps.heavy = L.heavy;
     e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
     PartSpec pr{1, sd.B, p.I, -1, 0, 1};
     pr.st = ctx->status;
+    pr.heavy = L.heavy;
     if (out->mode == MWJ_COUNT_GROUP_BY_A) {   // every a of R must lie in the group-by domain
         pr.dom = (uint32_t)out->a_domain;
     }
@@ -386,6 +399,12 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     g.build_s = lin_build_s(R.n, S.n);
     int mode = out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0;
     if ((e = lin_agg_launch(g, mode, st)) != cudaSuccess) return cuda_fail(ctx, e, "linear probe");
+    if (p.heavy) {   // the heavy-key bucket, after the I light ones
+        e = heavy_linear(L.Sp, L.offS, p.I * p.J, L.Rp, L.offR, p.I, L.heavy, g.t, L.hw, out->a_domain,
+                         mode == 1 ? (unsigned long long *)out->group_counts : nullptr,
+                         (unsigned long long *)out->total, ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "heavy keys");
+    }
     if (p.rows) {
         e = scan_excl_u64((const uint64_t *)L.rowcount, (uint64_t *)L.base, p.I, true, L.sscratch, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "row scan");

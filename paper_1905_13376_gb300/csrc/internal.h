@@ -13,6 +13,8 @@ namespace mwj {
 // bucket(t) = fastrange(mix32(key1 ^ seed1), P1) * P2 + fastrange(mix32(key2 ^ seed2), P2)
 // where key1/key2 are column col1/col2 (0 = x, 1 = y) of tuple t; col2 < 0
 // means a single level (P2 = 1).
+// With a heavy-key table (`heavy`, see skew.h), a tuple whose col1 value is a
+// heavy key goes to one extra bucket after the hashed ones (index Pbase()).
 struct PartSpec {
     int col1;
     uint32_t seed1, P1;
@@ -20,7 +22,9 @@ struct PartSpec {
     uint32_t seed2, P2;
     uint32_t dom = 0;     // when > 0: every x must lie in [0, dom), else MWJ_ERR_DOMAIN
     DevStatus *st = nullptr;
-    __host__ __device__ uint32_t P() const { return P1 * (col2 >= 0 ? P2 : 1u); }
+    const uint32_t *heavy = nullptr;   // device heavy-key table, or null
+    __host__ __device__ uint32_t Pbase() const { return P1 * (col2 >= 0 ? P2 : 1u); }
+    __host__ __device__ uint32_t P() const { return Pbase() + (heavy ? 1u : 0u); }
 };
 
 enum Payload { PAY_PAIR = 0, PAY_X = 1, PAY_Y = 2 };

@@ -22,6 +22,7 @@
 // The order of tuples inside a bucket is not specified (atomics decide it);
 // consumers never depend on it.
 #include "internal.h"
+#include "skew.h"
 
 namespace mwj {
 namespace {
@@ -32,8 +33,11 @@ constexpr int TILE = PT * IPT;        // 4096 tuples
 constexpr uint32_t kStagedMaxP = 4096;
 constexpr int kWarps = PT / 32;
 
-__device__ __forceinline__ uint32_t bucket_tuple(int32_t x, int32_t y, const PartSpec &sp) {
+// hs: the heavy-key table in shared memory, or null (no heavy keys)
+__device__ __forceinline__ uint32_t bucket_tuple(int32_t x, int32_t y, const PartSpec &sp,
+                                                 const uint32_t *hs) {
     int32_t k1 = sp.col1 ? y : x;
+    if (hs && heavy_slot(hs, (uint32_t)k1) >= 0) return sp.Pbase();
     uint32_t b = bucket_of(k1, sp.seed1, sp.P1);
     if (sp.col2 >= 0) {
         int32_t k2 = sp.col2 ? y : x;
@@ -63,6 +67,8 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
                                                   const int32_t *__restrict__ y, uint32_t n,
                                                   PartSpec sp, uint32_t tiles_per_cta,
                                                   uint32_t *__restrict__ counts) {
+    __shared__ uint32_t hbuf[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(sp.heavy, hbuf);
     extern __shared__ uint32_t hist[];
     const uint32_t P = sp.P();
     const uint32_t H = WARP_PRIVATE ? P * kWarps : P;
@@ -75,8 +81,8 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
     uint32_t i = c.begin + threadIdx.x * 4;
     // one atomic per run of equal buckets among 4 consecutive tuples
     auto count4 = [&](const int4 &xv, const int4 &yv) {
-        const uint32_t b0 = bucket_tuple(xv.x, yv.x, sp), b1 = bucket_tuple(xv.y, yv.y, sp),
-                       b2 = bucket_tuple(xv.z, yv.z, sp), b3 = bucket_tuple(xv.w, yv.w, sp);
+        const uint32_t b0 = bucket_tuple(xv.x, yv.x, sp, hs), b1 = bucket_tuple(xv.y, yv.y, sp, hs),
+                       b2 = bucket_tuple(xv.z, yv.z, sp, hs), b3 = bucket_tuple(xv.w, yv.w, sp, hs);
         uint32_t run = 1;
         if (b1 == b0) ++run; else { atomicAdd(&my[b0], run); run = 1; }
         if (b2 == b1) ++run; else { atomicAdd(&my[b1], run); run = 1; }
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(PT) k_part_hist(const int32_t *__restrict__ x,
         for (uint32_t k = i; k < i + 4 && k < c.end; ++k) {
             int32_t xv = (USE & 1) ? __ldg(x + k) : 0;
             int32_t yv = (USE & 2) ? __ldg(y + k) : 0;
-            atomicAdd(&my[bucket_tuple(xv, yv, sp)], 1u);
+            atomicAdd(&my[bucket_tuple(xv, yv, sp, hs)], 1u);
         }
     }
     __syncthreads();
@@ -174,6 +180,8 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
     const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
     uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
     typename PayT<PAY>::T *__restrict__ out) {
+    __shared__ uint32_t hbuf[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(sp.heavy, hbuf);
     using T = typename PayT<PAY>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t P = sp.P();
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
                 int j = h * 4 + k;
                 if (li + k < tn) {
                     if (sp.dom && (uint32_t)xs[k] >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xs[k]);
-                    bk[j] = bucket_tuple(xs[k], ys[k], sp);
+                    bk[j] = bucket_tuple(xs[k], ys[k], sp, hs);
                     rk[j] = atomicAdd(&cnt[bk[j]], 1u);
                     pv[j] = make_pay<PAY>(xs[k], ys[k]);
                 } else {
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_staged(
 // Carried tuples always lie in one sector, [gs, gs + carried): either the
 // run completes that sector (then all of them are written, W >= carried)
 // or nothing of the run is written and they stay in their carry slots.
-constexpr uint32_t kWcMaxP = 1024;
+constexpr uint32_t kWcMaxP = 1152;   // 1024 hashed buckets + a heavy-key bucket fit two CTAs per SM
 constexpr uint32_t kToCarry = 0x80000000u;   // gpos flag: carry slot, not an output position
 constexpr uint32_t kNoBucket = 0xFFFFu;      // past the end of a ragged tile
 
@@ -350,6 +358,8 @@ __global__ void __launch_bounds__(PT, 2) k_part_scatter_wc(
     const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
     uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
     typename PayT<PAY>::T *__restrict__ out) {
+    __shared__ uint32_t hbuf[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(sp.heavy, hbuf);
     using T = typename PayT<PAY>::T;
     constexpr uint32_t CARRY = wc_carry<PAY>();
     constexpr uint32_t SECT = CARRY + 1;   // tuples per 32-byte sector
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(PT, 2) k_part_scatter_wc(
             uint32_t b = kNoBucket;
             if (l < tn) {
                 if (sp.dom && (uint32_t)xs[j] >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xs[j]);
-                b = bucket_tuple(xs[j], ys[j], sp);
+                b = bucket_tuple(xs[j], ys[j], sp, hs);
             }
             const bool cont = (j & 3) && b == (br[j - 1 < 0 ? 0 : j - 1] >> 16);
             br[j] = (b << 16) | (cont ? (br[j - 1 < 0 ? 0 : j - 1] & 0xFFFFu) + 1u : 0u);   // place in its run
@@ -494,6 +504,8 @@ __global__ void __launch_bounds__(PT) k_part_scatter_direct(
     const int32_t *__restrict__ x, const int32_t *__restrict__ y, uint32_t n, PartSpec sp,
     uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
     typename PayT<PAY>::T *__restrict__ out) {
+    __shared__ uint32_t hbuf[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(sp.heavy, hbuf);
     extern __shared__ uint32_t cur[];
     const uint32_t P = sp.P();
     const uint32_t G = gridDim.x;
@@ -503,7 +515,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_direct(
     for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
         int32_t xv = __ldg(x + i), yv = __ldg(y + i);
         if (sp.dom && (uint32_t)xv >= sp.dom && sp.st) set_status(sp.st, MWJ_ERR_DOMAIN, xv);
-        uint32_t b = bucket_tuple(xv, yv, sp);
+        uint32_t b = bucket_tuple(xv, yv, sp, hs);
         uint32_t p = atomicAdd(&cur[b], 1u);
         out[p] = make_pay<PAY>(xv, yv);
     }
@@ -515,6 +527,8 @@ __global__ void __launch_bounds__(PT) k_part_scatter_z(
     const int32_t *__restrict__ x, const int32_t *__restrict__ y, const int32_t *__restrict__ z,
     uint32_t n, PartSpec sp, uint32_t tiles_per_cta, const uint32_t *__restrict__ scanned,
     uint2 *__restrict__ out, int32_t *__restrict__ outz) {
+    __shared__ uint32_t hbuf[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(sp.heavy, hbuf);
     extern __shared__ uint32_t cur[];
     const uint32_t P = sp.P();
     const uint32_t G = gridDim.x;
@@ -523,7 +537,7 @@ __global__ void __launch_bounds__(PT) k_part_scatter_z(
     Chunk c = cta_chunk(n, tiles_per_cta);
     for (uint32_t i = c.begin + threadIdx.x; i < c.end; i += PT) {
         int32_t xv = __ldg(x + i), yv = __ldg(y + i);
-        uint32_t b = bucket_tuple(xv, yv, sp);
+        uint32_t b = bucket_tuple(xv, yv, sp, hs);
         uint32_t p = atomicAdd(&cur[b], 1u);
         out[p] = make_uint2((uint32_t)xv, (uint32_t)yv);
         outz[p] = __ldg(z + i);

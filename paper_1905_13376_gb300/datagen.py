@@ -31,6 +31,9 @@ Workload recipes (sizes as in the headline configurations):
   [0, 2^16); the fact relation S(B,C) of 2^26 tuples holds foreign keys
   drawn uniformly (or Zipf(1.0) through a bijection) from the dimension
   keys, sorted by B like lineitem is by orderkey.
+* ``skewed_linear``: R(A,B), S(B,C), T(C,D) whose B column is Zipf(s) in
+  both R and S through one shared key bijection (heavy keys join each other),
+  the other columns uniform; the skewed inputs of Section 7's future work.
 * ``batched_queries``: many small independent joins with log-uniform sizes
   and key domains, keys uniform or Zipf(1.0) (P(k) proportional to
   1/(k+1), then mapped through a bijection of the domain).
@@ -199,6 +202,32 @@ def _keys(g, n: int, domain: int, zipf: bool, s: float = 1.0) -> np.ndarray:
             break
     off = int(g.integers(0, domain))
     return ((k * mult + off) % domain).astype(np.int32)
+
+
+def skewed_linear(n: int = 1 << 22, s: float = 1.5, b_domain: int = 1 << 20,
+                  c_domain: int = 1 << 22, a_domain: int = 1 << 20, seed: int = SEED_BASE + 6):
+    """R(A,B), S(B,C), T(C,D) of n tuples each whose join column B is Zipf(s)
+    in both R and S through one shared bijection of [0, b_domain) (so the
+    heavy keys of R and S are the same keys); A, C, D uniform.  Stands in for
+    the skewed inputs the paper leaves to future work."""
+    g = _rng(seed)
+    H = _harmonic(s, max(b_domain, 1 << 20))[:b_domain]
+    while True:
+        mult = int(g.integers(1, max(2, b_domain)))
+        if math.gcd(mult, b_domain) == 1:
+            break
+    off = int(g.integers(0, b_domain))
+
+    def zipf_b():
+        k = np.searchsorted(H, g.random(n) * H[-1], side="right")
+        k = np.minimum(k, b_domain - 1).astype(np.int64)
+        return ((k * mult + off) % b_domain).astype(np.int32)
+
+    R = (g.integers(0, a_domain, n, dtype=np.int64).astype(np.int32), zipf_b())
+    S = (zipf_b(), g.integers(0, c_domain, n, dtype=np.int64).astype(np.int32))
+    T = (g.integers(0, c_domain, n, dtype=np.int64).astype(np.int32),
+         g.integers(0, a_domain, n, dtype=np.int64).astype(np.int32))
+    return R, S, T
 
 
 def star_schema(n_fact: int = 1 << 26, n_dim: int = 1 << 20, attr_domain: int = 1 << 16,

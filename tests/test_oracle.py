@@ -253,3 +253,19 @@ def test_binary_count(oracle_lib):
     S = rand_rel(g, 40, 4, 5)
     brute = sum(1 for b in R[1] for b2 in S[0] if b == b2)
     assert oracle.binary_count(R, S) == brute
+
+
+def test_factorised_group_by_matches_oracle(oracle_lib):
+    """The factorised form the full-size skew test uses, against the oracle
+    on skewed inputs (heavy keys shared by R and S) and on the uniform config."""
+    from factorised import factorised_group_by
+    from paper_1905_13376_gb300 import datagen
+    for R, S, T, dom in [
+        datagen.skewed_linear(n=1 << 14, s=1.3, b_domain=1 << 11, c_domain=1 << 10,
+                              a_domain=1 << 9, seed=77) + (1 << 9,),
+        datagen.linear_uniform(n=4000, ad=1 << 9, bd=64, cd=64, dd=100, seed=5) + (1 << 9,),
+    ]:
+        want = oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=dom)
+        total, cnt = factorised_group_by(R, S, T, dom)
+        assert total == want["total"]
+        assert np.array_equal(cnt, want["counts"])
