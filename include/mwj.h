@@ -154,6 +154,21 @@ mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
 mwj_status mwj_join3_star(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, const mwj_shares *shares,
                           const mwj_out *out, void *workspace, size_t ws_bytes, void *stream);
 
+/* Chain of four relations R(A,B) S(B,C) T(C,D) U(D,E), COUNT or COUNT
+ * GROUP BY A (the "additional levels of hashing" of Section 7): one hash
+ * level per join attribute.  U becomes an on-chip table of deg_U(d), T a
+ * table of w_T(c) = sum of deg_U(d) over T's (c,d), and R and S are joined
+ * on B as in mwj_join3_linear with w_T(c) in place of T's degree; no
+ * intermediate relation is materialised.  shares: s[0] = H(B) buckets,
+ * s[1] must be 1, s[2] = log2 of the on-chip table slots (as for the linear
+ * join); NULL = the linear join's default.  MATERIALIZE is not offered
+ * (MWJ_ERR_INVALID_ARG).  workspace: >= mwj_join4_workspace_size(...). */
+mwj_status mwj_join4_workspace_size(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, mwj_rel U,
+                                    const mwj_shares *shares, mwj_mode mode, size_t *bytes);
+mwj_status mwj_join4_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, mwj_rel U,
+                            const mwj_shares *shares, const mwj_out *out, void *workspace,
+                            size_t ws_bytes, void *stream);
+
 /* Cascade of binary hash joins (Section 6.3): I(A,B,C) = R join S is
  * materialised in the workspace (in chunks when it does not fit), then
  * I join T gives the same result as the 3-way join.  kind = MWJ_LINEAR or

@@ -85,6 +85,11 @@ _SIGS = {
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_join3_star": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
                                       ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_join4_workspace_size": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, mwj_rel,
+                                                ctypes.POINTER(mwj_shares), ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "mwj_join4_linear": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
+                                        ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
@@ -304,6 +309,24 @@ class Context:
         None for the default."""
         return self._run(self.lib.mwj_join3_star, MWJ_STAR, R, S, T, mode, shares, a_domain,
                          capacity, 4, stream, sync)
+
+    def join4_linear(self, R, S, T, U, mode="count", shares=None, a_domain=None, stream=None,
+                     sync=True):
+        """Chain of four relations R(A,B) S(B,C) T(C,D) U(D,E): COUNT or
+        COUNT GROUP BY A."""
+        if isinstance(mode, str):
+            mode = MODES[mode]
+        o, res = self._outputs(mode, a_domain, 0, 4)
+        nb = ctypes.c_size_t(0)
+        self._check(self.lib.mwj_join4_workspace_size(self.h, _rel(R), _rel(S), _rel(T), _rel(U),
+                                                      _shares(shares), int(mode), ctypes.byref(nb)))
+        ws = self.workspace(nb.value)
+        self._check(self.lib.mwj_join4_linear(self.h, _rel(R), _rel(S), _rel(T), _rel(U), _shares(shares),
+                                              ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                              self._stream(stream)))
+        if sync:
+            self._check(self.lib.mwj_stream_status(self.h, self._stream(stream)))
+        return res
 
     def join3_cyclic(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
                      stream=None, sync=True):

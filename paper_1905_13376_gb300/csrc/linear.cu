@@ -17,6 +17,8 @@
 // order.  If R_i holds more distinct B values than the table can keep, the
 // CTA processes R_i in chunks, each followed by its own pass over S_i; the
 // join distributes over the union of the chunks, so the result is unchanged.
+#include <type_traits>
+
 #include "internal.h"
 #include "linear.h"
 #include "tables.h"
@@ -420,6 +422,38 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
     }
 }
 
+// T's weighted table (4-relation chain): 16-byte slots, word 0 = (1 << 32 |
+// c) when occupied (0 when empty), word 1 = the 64-bit weight of c.  The
+// first probes of a batch read word 0 only; the weight is read from the
+// found slot (same sector).
+__device__ __forceinline__ void tw_issue(const unsigned long long *tw, uint32_t seed, uint32_t mask,
+                                         const uint2 (&t)[NB], const bool (&use)[NB], uint32_t (&ts)[NB],
+                                         unsigned long long (&v)[NB]) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (use[k]) {
+            ts[k] = slot_of(t[k].y, seed, mask);
+            v[k] = __ldg(tw + 2 * (size_t)ts[k]);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long tw_resolve(const unsigned long long *tw, uint32_t mask,
+                                                         uint32_t c, uint32_t s, unsigned long long x) {
+    const unsigned long long want = (1ull << 32) | c;
+    for (uint32_t it = 0; it < mask && x != 0ull && x != want; ++it) {
+        s = (s + 1) & mask;
+        x = __ldg(tw + 2 * (size_t)s);
+    }
+    return x == want ? __ldg(tw + 2 * (size_t)s + 1) : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long tw_weight(const unsigned long long *tw, uint32_t seed,
+                                                        uint32_t mask, uint32_t c) {
+    const uint32_t s = slot_of(c, seed, mask);
+    return tw_resolve(tw, mask, c, s, __ldg(tw + 2 * (size_t)s));
+}
+
 // The same two aggregates with S_i as the on-chip side.  The B-keyed table
 // of CTA i gathers w(b) = sum of deg_T(c) over the tuples (b, c) of S_i while
 // S_i streams in once; then R_i streams past it once, adding w(b) to total
@@ -428,8 +462,11 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg(LinArgs g) {
 // flush); in exchange every S tuple pays its T lookup whether or not its b
 // occurs in R_i.  When S_i holds more distinct B values than the table
 // keeps, S_i is taken in chunks, each followed by its own pass over R_i.
-template <int MODE>
+// WT: T's table holds 64-bit weights w_T(c) instead of degrees (the chain
+// of four relations, where w_T(c) = sum of deg_U(d) over T's (c, d)).
+template <int MODE, bool WT>
 __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
+    using TW = typename std::conditional<WT, unsigned long long, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t cap = 1u << g.cap_log2;
     const size_t arr = align256((cap + 1) * sizeof(uint32_t));
@@ -442,7 +479,7 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
     const uint32_t i = blockIdx.x;
     const uint32_t r0 = g.offR[i], r1 = g.offR[i + 1];
     const uint32_t s0 = g.offS[(size_t)i * g.JS], s1 = g.offS[(size_t)(i + 1) * g.JS];
-    const uint32_t tmask = (g.t.J == 0) ? __ldg(g.t.meta) : 0u;
+    const uint32_t tmask = WT ? __ldg(g.tw_meta) : (g.t.J == 0) ? __ldg(g.t.meta) : 0u;
     const uint32_t mask = cap - 1;
     unsigned long long acc = 0;
 
@@ -459,7 +496,7 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
         __syncthreads();
     };
     // w[slot] += v for the batch's (slot, v), runs of equal slots merged
-    auto add_w = [&](const int (&sl)[NB], const uint32_t (&dT)[NB]) {
+    auto add_w = [&](const int (&sl)[NB], const TW (&dT)[NB]) {
         int cur = -1;
         unsigned long long run = 0;
 #pragma unroll
@@ -491,7 +528,9 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
                     for (int k = 0; k < NB; ++k) use[k] = k < (int)n;
                     uint32_t ts[NB];
                     unsigned long long v[NB];
-                    if (g.t.J == 0) t_issue(g.t, tmask, t, use, ts, v);   // in flight during the inserts
+                    // in flight during the inserts
+                    if (WT) tw_issue(g.tw, g.tw_seed, tmask, t, use, ts, v);
+                    else if (g.t.J == 0) t_issue(g.t, tmask, t, use, ts, v);
                     int sl[NB];
                     bool failed = false;
 #pragma unroll
@@ -511,14 +550,19 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
                         atomicOr(&bad, 1u);
                         return;
                     }
-                    uint32_t dT[NB];
-                    if (g.t.J == 0) {
+                    TW dT[NB];
+                    if (WT) {
 #pragma unroll
                         for (int k = 0; k < NB; ++k)
-                            dT[k] = use[k] ? t_resolve(g.t, tmask, t[k].y, ts[k], v[k]) : 0u;
+                            dT[k] = use[k] ? (TW)tw_resolve(g.tw, tmask, t[k].y, ts[k], v[k]) : (TW)0;
+                    } else if (g.t.J == 0) {
+#pragma unroll
+                        for (int k = 0; k < NB; ++k)
+                            dT[k] = use[k] ? (TW)t_resolve(g.t, tmask, t[k].y, ts[k], v[k]) : (TW)0;
                     } else {
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) dT[k] = use[k] ? timg_deg(g.t, (int32_t)t[k].y) : 0u;
+                        for (int k = 0; k < NB; ++k)
+                            dT[k] = use[k] ? (TW)timg_deg(g.t, (int32_t)t[k].y) : (TW)0;
                     }
                     add_w(sl, dT);
                 });
@@ -532,7 +576,9 @@ __global__ void __launch_bounds__(LT, 2) k_lin_agg_s(LinArgs g) {
             if (!ok)   // chunks built in bounded rounds, one T lookup per tuple
                 cend = build_chunk<true>(g.Sp, pos, s1, keys, cap, g.seed_slot, 0xFFFFFFFFu, &nd, g.st,
                                          [&](int slot, uint2 t) {
-                                             const uint32_t d = timg_deg(g.t, (int32_t)t.y);
+                                             const unsigned long long d =
+                                                 WT ? tw_weight(g.tw, g.tw_seed, tmask, t.y)
+                                                    : (unsigned long long)timg_deg(g.t, (int32_t)t.y);
                                              if (d) add_u64_split(&wlo[slot], &whi[slot], d);
                                          });
             // R_i streams past w: total += w(b), cnt[a] += w(b), runs of equal A merged
@@ -706,8 +752,10 @@ cudaError_t lin_agg_launch(const LinArgs &g, int mode, cudaStream_t st) {
     const size_t smem = lin_agg_smem(g.cap_log2, mode, g.build_s != 0);
     const char *name = mode == 1 ? "lin_probe_groupby" : "lin_probe_count";
     if (g.build_s)
-        return mode == 1 ? launch_agg(k_lin_agg_s<1>, g, smem, name, st)
-                         : launch_agg(k_lin_agg_s<0>, g, smem, name, st);
+        return g.tw ? (mode == 1 ? launch_agg(k_lin_agg_s<1, true>, g, smem, name, st)
+                                 : launch_agg(k_lin_agg_s<0, true>, g, smem, name, st))
+                    : (mode == 1 ? launch_agg(k_lin_agg_s<1, false>, g, smem, name, st)
+                                 : launch_agg(k_lin_agg_s<0, false>, g, smem, name, st));
     return mode == 1 ? launch_agg(k_lin_agg<1>, g, smem, name, st)
                      : launch_agg(k_lin_agg<0>, g, smem, name, st);
 }

@@ -21,6 +21,11 @@ struct LinArgs {
     DevStatus *st;
     uint32_t spin_limit;        // polls of a bounded barrier wait before MWJ_ERR_TIMEOUT
     uint32_t build_s;           // aggregates: 1 = S_i is the on-chip side, 0 = R_i (Algorithm 1)
+    // chain of four relations: T's weighted table (16-byte slots, see
+    // k_lin_agg_s) instead of T's degrees; null for the 3-way join
+    const unsigned long long *tw;
+    const uint32_t *tw_meta;    // tw_meta[0] = slot mask
+    uint32_t tw_seed;
 };
 
 // On-chip side of the aggregate kernels: S_i whenever |S| <= 2 |R|, so that

@@ -535,9 +535,8 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
 
 }  // namespace
 
-cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
-                                uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
-                                DevStatus *status, int num_sms, cudaStream_t st) {
+cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
+                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st) {
     cudaError_t e;
     const uint32_t nn = (uint32_t)n;
     const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
@@ -552,11 +551,18 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
         if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(done, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     }
-    {
-        ProfScope ps_("t_size", st);
-        k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor,
-                                                   meta);
-    }
+    ProfScope ps_("t_size", st);
+    k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
+                                uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
+                                DevStatus *status, int num_sms, cudaStream_t st) {
+    cudaError_t e;
+    const uint32_t nn = (uint32_t)n;
+    if ((e = single_table_size(keys, n, seed, hll_regs, meta, reserve_slots, num_sms, st)) != cudaSuccess)
+        return e;
     {
         ProfScope ps_("t_clear", st);
         k_tclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)tbl, meta);

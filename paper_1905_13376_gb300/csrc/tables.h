@@ -68,6 +68,10 @@ cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32
 cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
                                 DevStatus *status, int num_sms, cudaStream_t st);
+// Only the sizing step of single_table_direct: meta[0] = mask of a table of
+// 2^k >= 4 x (estimated distinct keys) slots (at most reserve_slots).
+cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
+                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st);
 uint32_t hll_registers();
 size_t hll_scratch_registers(int num_sms);
 // HyperLogLog registers of keys[0, n) into regs[0, hll_registers()); regs must
