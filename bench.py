@@ -260,6 +260,7 @@ def run_ours(args, rank, world, local_rank):
 
     star = None if args.no_star else run_star(ctx, stream, args, peaks())
     skew = None if args.no_skew else run_skew(ctx, stream, args)
+    join4 = None if args.no_join4 else run_join4(ctx, stream, args, F)
 
     # max over ranks
     if world > 1:
@@ -305,6 +306,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": tuples * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
         "gpu_launches": launches, "clocks": clocks, "cascade": casc, "star": star, "skew": skew,
+        "join4": join4,
     }
     return out, F
 
@@ -417,6 +419,32 @@ def run_skew(ctx, stream, args):
             "result_total": int(want.sum())}
 
 
+def run_join4(ctx, stream, args, F):
+    """F |x| F |x| F |x| F GROUP BY A on the benchmark graph: the chain one
+    relation longer, one more hash level (U's degrees, T's weights)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dF = tuple(torch.from_numpy(c).to(dev) for c in F)
+    adom = args.vertices
+    r = ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom)
+    exact_sum = int(r["counts"].sum().item()) == int(r["total"].item())
+    for _ in range(3):
+        ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom, sync=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = len(F[0])
+    return {"workload": "chain of four relations F|x|F|x|F|x|F, COUNT(*) GROUP BY A, same graph",
+            "value": 4 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "result_total": int(r["total"].item()), "group_sum_equals_total": bool(exact_sum)}
+
+
 def cpu_baseline(F, a_domain, budget_s=30.0):
     import oracle
     t0 = time.perf_counter()
@@ -464,6 +492,8 @@ def main():
                     help="I J [log2 table slots]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-join4", action="store_true",
+                    help="skip the four-relation chain arm")
     ap.add_argument("--no-skew", action="store_true",
                     help="skip the skewed-join arm (Zipf(1.5) join column, 2^22 tuples)")
     ap.add_argument("--no-star", action="store_true",

@@ -169,6 +169,25 @@ mwj_status mwj_join4_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, mwj_r
                             const mwj_shares *shares, const mwj_out *out, void *workspace,
                             size_t ws_bytes, void *stream);
 
+/* Flajolet-Martin sketches of the distinct friends of friends of friends of
+ * every A (Section 4.1's footnote; the approximate variant of Example 1):
+ * D(a) = { d : (a,b) in R, (b,c) in S, (c,d) in T } is summarised by a PCSA
+ * sketch of 16 bitmaps of 32 bits (value d sets bit rho(h div 16) of bitmap
+ * h mod 16, h = MurmurHash3's fmix32(d xor 0x5BD1E995), rho = index of the
+ * lowest 1 bit, 27 when h div 16 is 0); sketches are carried along the join
+ * with OR as counts are with +.  sketches: device, a_domain x 16 uint32,
+ * overwritten (sketch of a at [16 a, 16 a + 16)).  estimates: device,
+ * a_domain floats, or NULL: (16 / 0.77351) * 2^(mean over bitmaps of the
+ * index of their lowest 0 bit).  Every a of R must lie in [0, a_domain)
+ * (MWJ_ERR_DOMAIN from mwj_stream_status otherwise).  shares: s[0] = H(B)
+ * buckets (NULL: ~16K S tuples per bucket); the other entries are ignored.
+ * workspace: device, >= mwj_fm_workspace_size(...). */
+mwj_status mwj_fm_workspace_size(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
+                                 const mwj_shares *shares, size_t *bytes);
+mwj_status mwj_fm_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, const mwj_shares *shares,
+                         int32_t a_domain, uint32_t *sketches, float *estimates, void *workspace,
+                         size_t ws_bytes, void *stream);
+
 /* Cascade of binary hash joins (Section 6.3): I(A,B,C) = R join S is
  * materialised in the workspace (in chunks when it does not fit), then
  * I join T gives the same result as the 3-way join.  kind = MWJ_LINEAR or

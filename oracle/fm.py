@@ -111,3 +111,31 @@ def sketches(R, S, T, a_domain: int):
         sk[a] = sketch_of(ds)
         n[a] = len(ds)
     return sk, n
+
+
+def _csr(x, y):
+    """key -> values as (sorted unique keys, starts, values grouped by key)."""
+    x = np.asarray(x, dtype=np.int64)
+    y = np.asarray(y, dtype=np.int64)
+    o = np.argsort(x, kind="stable")
+    keys, starts = np.unique(x[o], return_index=True)
+    return keys, np.append(starts, len(x)), y[o]
+
+
+def _expand(csr, vals):
+    """The set of values reached from the keys `vals` through one relation."""
+    keys, starts, out = csr
+    vals = np.unique(np.asarray(vals, dtype=np.int64))
+    p = np.searchsorted(keys, vals)
+    inside = p < len(keys)
+    p, vals = p[inside], vals[inside]
+    p = p[keys[p] == vals]
+    parts = [out[starts[i]:starts[i + 1]] for i in p]
+    return np.unique(np.concatenate(parts)) if parts else np.zeros(0, np.int64)
+
+
+def fof3_sets_csr(R, S, T, a_values):
+    """D(a) for each a (numpy arrays), the same sets as fof3_sets, for
+    relations too large for Python dictionaries."""
+    Rc, Sc, Tc = _csr(*R), _csr(*S), _csr(*T)
+    return {int(a): _expand(Tc, _expand(Sc, _expand(Rc, [a]))) for a in a_values}

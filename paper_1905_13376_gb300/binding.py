@@ -90,6 +90,10 @@ _SIGS = {
                                                 ctypes.POINTER(ctypes.c_size_t)]),
     "mwj_join4_linear": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
+    "mwj_fm_workspace_size": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares),
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "mwj_fm_linear": (ctypes.c_int, [_P, mwj_rel, mwj_rel, mwj_rel, ctypes.POINTER(mwj_shares), ctypes.c_int32,
+                                     _P, _P, _P, ctypes.c_size_t, _P]),
     "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
@@ -327,6 +331,26 @@ class Context:
         if sync:
             self._check(self.lib.mwj_stream_status(self.h, self._stream(stream)))
         return res
+
+    def fm_linear(self, R, S, T, a_domain, shares=None, estimates=True, stream=None, sync=True):
+        """Flajolet-Martin (PCSA) sketches of the distinct D reachable from
+        every A through R(A,B) S(B,C) T(C,D): {"sketches": int32
+        (a_domain, 16) holding the uint32 bitmaps, "estimates": float32
+        (a_domain,) or None}."""
+        import torch
+        sk = torch.empty((int(a_domain), 16), dtype=torch.int32, device=self.device)
+        est = torch.empty(int(a_domain), dtype=torch.float32, device=self.device) if estimates else None
+        nb = ctypes.c_size_t(0)
+        self._check(self.lib.mwj_fm_workspace_size(self.h, _rel(R), _rel(S), _rel(T), _shares(shares),
+                                                   ctypes.byref(nb)))
+        ws = self.workspace(nb.value)
+        self._check(self.lib.mwj_fm_linear(self.h, _rel(R), _rel(S), _rel(T), _shares(shares), int(a_domain),
+                                           ctypes.c_void_p(sk.data_ptr()),
+                                           ctypes.c_void_p(est.data_ptr()) if est is not None else None,
+                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), self._stream(stream)))
+        if sync:
+            self._check(self.lib.mwj_stream_status(self.h, self._stream(stream)))
+        return {"sketches": sk, "estimates": est}
 
     def join3_cyclic(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
                      stream=None, sync=True):

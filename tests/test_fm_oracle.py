@@ -73,3 +73,15 @@ def test_union_is_or_and_duplicates_ignored():
     assert np.array_equal(fm.sketch_of(np.concatenate([A, B])), fm.sketch_of(A) | fm.sketch_of(B))
     assert np.array_equal(fm.sketch_of(np.concatenate([A, A])), fm.sketch_of(A))
     assert fm.estimate(np.zeros(fm.M, np.uint32)) == pytest.approx(fm.M / fm.PHI)
+
+
+def test_csr_sets_match_plain_sets():
+    g = np.random.default_rng(4)
+    for _ in range(40):
+        n = [int(g.integers(0, 60)) for _ in range(3)]
+        R = (g.integers(-3, 6, n[0]), g.integers(-3, 9, n[0]))
+        S = (g.integers(-3, 9, n[1]), g.integers(-3, 9, n[1]))
+        T = (g.integers(-3, 9, n[2]), g.integers(0, 20, n[2]))
+        plain = fm.fof3_sets(R, S, T, range(-3, 6))
+        csr = fm.fof3_sets_csr(R, S, T, range(-3, 6))
+        assert all(set(csr[a].tolist()) == plain[a] for a in plain)
