@@ -261,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
     star = None if args.no_star else run_star(ctx, stream, args, peaks())
     skew = None if args.no_skew else run_skew(ctx, stream, args)
     join4 = None if args.no_join4 else run_join4(ctx, stream, args, F)
+    fmr = None if args.no_fm else run_fm(ctx, stream, args, F)
 
     # max over ranks
     if world > 1:
@@ -306,7 +307,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": tuples * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
         "gpu_launches": launches, "clocks": clocks, "cascade": casc, "star": star, "skew": skew,
-        "join4": join4,
+        "join4": join4, "fm": fmr,
     }
     return out, F
 
@@ -445,6 +446,34 @@ def run_join4(ctx, stream, args, F):
             "result_total": int(r["total"].item()), "group_sum_equals_total": bool(exact_sum)}
 
 
+def run_fm(ctx, stream, args, F):
+    """Flajolet-Martin sketches of every person's distinct friends of friends
+    of friends on the benchmark graph (the approximate query of the paper's
+    Section 4.1 footnote)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dF = tuple(torch.from_numpy(c).to(dev) for c in F)
+    adom = args.vertices
+    r = ctx.fm_linear(dF, dF, dF, adom)
+    for _ in range(3):
+        ctx.fm_linear(dF, dF, dF, adom, sync=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.fm_linear(dF, dF, dF, adom, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = len(F[0])
+    est = r["estimates"]
+    return {"workload": "distinct friends of friends of friends per person, PCSA sketches "
+                        "(16 x 32-bit bitmaps), F|x|F|x|F on the same graph",
+            "value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "median_estimate": float(est.median().item()), "max_estimate": float(est.max().item())}
+
+
 def cpu_baseline(F, a_domain, budget_s=30.0):
     import oracle
     t0 = time.perf_counter()
@@ -492,6 +521,8 @@ def main():
                     help="I J [log2 table slots]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-fm", action="store_true",
+                    help="skip the Flajolet-Martin sketch arm")
     ap.add_argument("--no-join4", action="store_true",
                     help="skip the four-relation chain arm")
     ap.add_argument("--no-skew", action="store_true",
