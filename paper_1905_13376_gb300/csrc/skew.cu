@@ -28,31 +28,33 @@ namespace mwj {
 namespace {
 
 constexpr int DT = 1024;                 // detection: one CTA
-constexpr uint32_t kSample = 4096;       // sampled tuples per relation
-constexpr uint32_t kCountSlots = 16384;  // sample count table (shared memory), at most half full
+constexpr uint32_t kSample = 2048;       // sampled tuples per relation
+constexpr uint32_t kCountSlots = 8192;   // sample count table (shared memory), at most half full
+constexpr uint32_t kMinCount = 8;        // a heavy key is seen at least this often in its sample
 constexpr uint32_t kPerThread = kSample / DT;
 constexpr int HT = 512;                  // heavy-bucket kernels: threads per CTA
 
 // One CTA: count a strided sample of each B column (kSample tuples, every
 // thread's loads in flight together) in a shared table of (key, count in R,
-// count in S); keys whose count reaches the threshold of their relation go
-// into the heavy table.  The sample decides only which keys take the heavy
-// path, never the join's result: a key with a 1/256 share of a relation is
-// sampled ~16 times, one at the threshold (half an average bucket) ~4 times.
+// count in S, packed in one word); keys whose count reaches the threshold of
+// their relation go into the heavy table.  The sample decides only which
+// keys take the heavy path, never the join's result.  The threshold is half
+// an average bucket and at least kMinCount sampled tuples (a 0.4% share): a
+// key far below it -- a hub of a power-law graph holds ~1e-4 of the edges --
+// is practically never sampled that often, so inputs without heavy keys keep
+// an empty table and the partitioner skips the per-tuple check.
 __global__ void __launch_bounds__(DT) k_heavy_detect(const int32_t *__restrict__ rb, uint32_t nR,
                                                      const int32_t *__restrict__ sb, uint32_t nS,
                                                      uint32_t I, uint32_t *__restrict__ heavy,
                                                      unsigned long long *__restrict__ hw) {
     extern __shared__ uint32_t sm[];
     uint32_t *key = sm;                      // kCountSlots
-    uint32_t *cR = key + kCountSlots;        // kCountSlots
-    uint32_t *cS = cR + kCountSlots;         // kCountSlots
-    uint32_t *ht = cS + kCountSlots;         // kHeavySlots
+    uint32_t *cnt = key + kCountSlots;       // kCountSlots: count in R | count in S << 16
+    uint32_t *ht = cnt + kCountSlots;        // kHeavySlots
     __shared__ uint32_t nh;
     for (uint32_t i = threadIdx.x; i < kCountSlots; i += DT) {
         key[i] = kEmptyKey;
-        cR[i] = 0;
-        cS[i] = 0;
+        cnt[i] = 0;
     }
     for (uint32_t i = threadIdx.x; i < kHeavySlots; i += DT) {
         ht[i] = kEmptyKey;
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(DT) k_heavy_detect(const int32_t *__restrict__
     }
     if (threadIdx.x == 0) nh = 0;
     __syncthreads();
-    auto count = [&](const int32_t *col, uint32_t n, uint32_t *cnt) {
+    auto count = [&](const int32_t *col, uint32_t n, uint32_t one) {
         const uint32_t m = n < kSample ? n : kSample;
         uint32_t ks[kPerThread];
 #pragma unroll
@@ -80,22 +82,22 @@ __global__ void __launch_bounds__(DT) k_heavy_detect(const int32_t *__restrict__
                     if (held == kEmptyKey) held = k;
                 }
                 if (held == k) {
-                    atomicAdd(&cnt[s], 1u);
+                    atomicAdd(&cnt[s], one);
                     break;
                 }
                 s = (s + 1) & (kCountSlots - 1);
             }
         }
     };
-    count(rb, nR, cR);
-    count(sb, nS, cS);
+    count(rb, nR, 1u);
+    count(sb, nS, 1u << 16);
     __syncthreads();
-    // share >= 1 / (2 I) of the sample, and at least 4 sampled tuples
+    // share >= 1 / (2 I) of the sample, and at least kMinCount sampled tuples
     const uint32_t mR = nR < kSample ? nR : kSample, mS = nS < kSample ? nS : kSample;
-    const uint32_t tR = max(4u, mR / (2u * I)), tS = max(4u, mS / (2u * I));
+    const uint32_t tR = max(kMinCount, mR / (2u * I)), tS = max(kMinCount, mS / (2u * I));
     for (uint32_t i = threadIdx.x; i < kCountSlots; i += DT) {
         const uint32_t k = key[i];
-        if (k == kEmptyKey || (cR[i] < tR && cS[i] < tS)) continue;
+        if (k == kEmptyKey || ((cnt[i] & 0xFFFFu) < tR && (cnt[i] >> 16) < tS)) continue;
         if (atomicAdd(&nh, 1u) >= kHeavyMax) continue;
         // at most kHeavyMax = kHeavySlots / 2 keys: a free slot is always found
         uint32_t s = slot_of(k, kHeavySeed, kHeavySlots - 1);
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(HT) k_heavy_r(const uint2 *__restrict__ Rp, co
 
 cudaError_t heavy_detect(const int32_t *rb, int64_t nR, const int32_t *sb, int64_t nS, uint32_t I,
                          uint32_t *heavy, unsigned long long *hw, cudaStream_t st) {
-    const size_t smem = (3 * (size_t)kCountSlots + kHeavySlots) * sizeof(uint32_t);
+    const size_t smem = (2 * (size_t)kCountSlots + kHeavySlots) * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_heavy_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfScope ps_("heavy_detect", st);

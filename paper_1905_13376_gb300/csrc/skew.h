@@ -15,7 +15,10 @@ constexpr uint32_t kHeavySeed = 0x2545F491u;
 constexpr size_t kHeavyTableWords = kHeavySlots + 4;
 
 // Slot of key k in the heavy table (a copy in shared memory), -1 if absent.
-__device__ __forceinline__ int heavy_slot(const uint32_t *hs, uint32_t k) {
+// Not inlined: the partition kernels call it only when the table holds keys,
+// and an inlined probe loop at every bucket computation of their unrolled
+// loops would crowd the instruction cache of the common, heavy-free case.
+static __device__ __noinline__ int heavy_slot(const uint32_t *hs, uint32_t k) {
     if (k == kEmptyKey) return -1;
     uint32_t s = slot_of(k, kHeavySeed, kHeavySlots - 1);
     for (uint32_t it = 0; it < kHeavySlots; ++it) {
