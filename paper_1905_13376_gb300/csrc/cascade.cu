@@ -780,7 +780,10 @@ extern "C" mwj_status mwj_cascade_join(mwj_ctx *ctx, int kind, mwj_rel R, mwj_re
             // cyclic: I by the same hash of (C, A) as T, then bucket-wise probes
             e = part_run(L.Ic, L.Ia, (int64_t)nI, p2, PAY_PAIR, L.I2, L.offI2, L.pscratch,
                          L.pscratch_bytes, sms, st, rows ? L.Ib : nullptr, rows ? L.Ib2 : nullptr);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "partition I");
+            if (e != cudaSuccess)
+                return fail(ctx, MWJ_ERR_CUDA, "partition I: %s (%llu rows into %u x %u buckets, scratch %zu of %zu)",
+                            cudaGetErrorString(e), (unsigned long long)nI, p.P2a, p.P2b, L.pscratch_bytes,
+                            part_scratch_bytes((int64_t)nI, p.P2a * p.P2b, sms));
             if (n2 == 0) {
                 c0 = c1;
                 continue;

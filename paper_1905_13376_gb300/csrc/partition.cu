@@ -600,9 +600,14 @@ cudaError_t scatter_launch(const int32_t *x, const int32_t *y, uint32_t n, const
 
 }  // namespace
 
+// Sized for the largest grid any n' <= n can get, min(tiles(n), max CTAs),
+// so a workspace sized for n serves every smaller call (geometry()'s own G is
+// not monotone in n: rounding tiles per CTA up can leave fewer CTAs).
 size_t part_scratch_bytes(int64_t n, uint32_t P, int num_sms) {
-    Geometry g = geometry(n, num_sms * 4);
-    size_t cnt = (size_t)P * g.G;
+    uint64_t tiles = ((uint64_t)(n > 0 ? n : 0) + TILE - 1) / TILE;
+    if (tiles == 0) tiles = 1;
+    const uint64_t gmax = (uint64_t)(num_sms > 0 ? num_sms : 1) * 4;
+    const size_t cnt = (size_t)P * (size_t)(tiles < gmax ? tiles : gmax);
     return align256(cnt * sizeof(uint32_t)) + scan_scratch_bytes(cnt);
 }
 

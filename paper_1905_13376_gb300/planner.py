@@ -352,12 +352,22 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--out", default="planner_run")
     ap.add_argument("--seed", type=int, default=1905)
+    ap.add_argument("--eval-only", action="store_true",
+                    help="time the held-out instances on this engine and score the packaged weights")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     log = lambda m: print(m, flush=True)
     torch.cuda.set_device(0)
     ctx = binding.Context(0)
     t0 = time.time()
+    if args.eval_only:
+        Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
+        summary, _ = evaluate(default_planner(ctx), Fev, tev)
+        rep = {"n_eval": len(Fev), "eval": summary, "collect_seconds": time.time() - t0,
+               "weights": "packaged planner_weights.npz"}
+        json.dump(rep, open(os.path.join(args.out, "report_eval.json"), "w"), indent=1)
+        log(json.dumps(rep, indent=1))
+        return
     Ftr, ttr, _, mtr, rej = collect(ctx, args.train, args.seed, args.budget, log, size_hi=args.size_hi)
     log(f"train: {len(Ftr)} instances in {time.time() - t0:.0f} s ({rej} rejected)")
     Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
