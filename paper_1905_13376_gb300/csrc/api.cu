@@ -87,6 +87,7 @@ struct LinLayout {
     uint32_t *ekey, *ecnt, *ecount, *meta;
     unsigned int *hll;
     void *pscratch; size_t pscratch_bytes;
+    void *pscratchR;   // single mode: R's own partition scratch (R is partitioned on the side stream)
     unsigned long long *rowcount, *base; void *sscratch;
 };
 
@@ -142,6 +143,7 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
     if (ps3 > ps) ps = ps3;
     L.pscratch = A.take<char>(ps);
     L.pscratch_bytes = ps;
+    L.pscratchR = p.single ? A.take<char>(ps) : nullptr;
     return A.used;
 }
 
@@ -223,12 +225,33 @@ mwj_status mwj_create(mwj_ctx **out, const mwj_config *cfg) {
     if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
     e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
     if (e != cudaSuccess) { cudaFree(ctx->status); delete ctx; return MWJ_ERR_CUDA; }
+    ctx->side = ctx->side2 = nullptr;
+    ctx->fork = ctx->join = ctx->join2 = ctx->heavy_ready = nullptr;
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->join2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->heavy_ready, cudaEventDisableTiming) != cudaSuccess) {
+        mwj_destroy(ctx);
+        return MWJ_ERR_CUDA;
+    }
     *out = ctx;
     return MWJ_OK;
 }
 
 mwj_status mwj_destroy(mwj_ctx *ctx) {
     if (!ctx) return MWJ_ERR_INVALID_ARG;
+    for (cudaStream_t s : {ctx->side, ctx->side2}) {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+    if (ctx->join2) cudaEventDestroy(ctx->join2);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->heavy_ready) cudaEventDestroy(ctx->heavy_ready);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;
     return MWJ_OK;
@@ -343,8 +366,31 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
         (e = cudaMemsetAsync(out->group_counts, 0, sizeof(int64_t) * (size_t)out->a_domain, st)) !=
             cudaSuccess)
         return cuda_fail(ctx, e, "memset group_counts");
-    // Algorithm 1, steps 1-3: T by g(C), S by (H(B), g(C)), R by H(B).  With
-    // one g(C) bucket T is not partitioned: its C table is built directly.
+    // With one g(C) bucket T is not partitioned: its C table is built
+    // directly, on a side stream, while S is partitioned here and R on a
+    // second side stream.
+    // On every return after the fork the caller's stream waits for the side
+    // stream, so no work of this call outlives it on the caller's stream.
+    struct JoinGuard {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        bool armed;
+        ~JoinGuard() {
+            if (armed) cudaStreamWaitEvent(st, ev, 0);
+        }
+    } join_guard{st, ctx->join, false}, join_guard2{st, ctx->join2, false};
+    if (p.single) {
+        if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "fork");
+        e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
+                                ctx->status, ctx->dev.num_sms, ctx->side);
+        const cudaError_t ej = cudaEventRecord(ctx->join, ctx->side);   // whatever was queued
+        if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
+        join_guard.armed = true;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "T tables");
+    }
+    // Algorithm 1, steps 1-3: T by g(C), S by (H(B), g(C)), R by H(B).
     if (!p.single) {
         PartSpec pt{0, sd.C, p.JT, -1, 0, 1};
         pt.st = ctx->status;
@@ -355,26 +401,40 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     // heavy B keys (aggregates): named from samples of R's and S's B columns
     if (p.heavy && (e = heavy_detect(R.y, R.n, S.x, S.n, p.I, L.heavy, L.hw, st)) != cudaSuccess)
         return cuda_fail(ctx, e, "heavy keys");
+    // single mode: R is partitioned on the second side stream (its own
+    // scratch) once the heavy keys are known, while S is partitioned here
+    PartSpec pr{1, sd.B, p.I, -1, 0, 1};
+    pr.st = ctx->status;
+    pr.heavy = L.heavy;
+    if (out->mode == MWJ_COUNT_GROUP_BY_A) pr.dom = (uint32_t)out->a_domain;   // every a of R in the domain
+    if (p.single) {
+        if ((e = cudaEventRecord(ctx->heavy_ready, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side2, ctx->heavy_ready, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "fork");
+        e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratchR, L.pscratch_bytes,
+                     ctx->dev.num_sms, ctx->side2);
+        const cudaError_t ej = cudaEventRecord(ctx->join2, ctx->side2);
+        if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
+        join_guard2.armed = true;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
+    }
     PartSpec ps{0, sd.B, p.I, p.J > 1 ? 1 : -1, sd.C, p.J};
     ps.st = ctx->status;
     ps.heavy = L.heavy;
     e = part_run(S.x, S.y, S.n, ps, PAY_PAIR, L.Sp, L.offS, L.pscratch, L.pscratch_bytes,
                  ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition S");
-    PartSpec pr{1, sd.B, p.I, -1, 0, 1};
-    pr.st = ctx->status;
-    pr.heavy = L.heavy;
-    if (out->mode == MWJ_COUNT_GROUP_BY_A) {   // every a of R must lie in the group-by domain
-        pr.dom = (uint32_t)out->a_domain;
+    if (!p.single) {
+        e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
+                     ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
     }
-    e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratch, L.pscratch_bytes,
-                 ctx->dev.num_sms, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");
     // T's tables
-    if (p.single)
-        e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
-                                ctx->status, ctx->dev.num_sms, st);
-    else
+    if (p.single) {
+        e = cudaStreamWaitEvent(st, ctx->join, 0);   // T's table is ready
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join2, 0);   // and R's partitions
+        join_guard.armed = join_guard2.armed = false;
+    } else
         e = tables_build(L.Tk, L.Tp, L.offT, p.JT, sd.slot2, L.img, L.capT, L.startT, L.dlist,
                          ctx->status, ctx->dev.num_sms, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "T tables");

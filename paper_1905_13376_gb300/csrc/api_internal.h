@@ -15,6 +15,11 @@ struct mwj_ctx {
     int64_t spin_limit;
     uint32_t cap_log2;        // on-chip R table size (log2 slots)
     mwj::DevStatus *status;   // device status word
+    // work of one call that shares no buffer with the rest (T's table while
+    // R and S are partitioned) runs on `side`, forked from and joined back
+    // to the caller's stream with these events
+    cudaStream_t side, side2;
+    cudaEvent_t fork, join, join2, heavy_ready;
     mwj::Profiler prof;
     char err[512];
 };
