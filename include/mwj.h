@@ -175,8 +175,9 @@ mwj_status mwj_join4_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, mwj_r
  * sketch of 16 bitmaps of 32 bits (value d sets bit rho(h div 16) of bitmap
  * h mod 16, h = MurmurHash3's fmix32(d xor 0x5BD1E995), rho = index of the
  * lowest 1 bit, 27 when h div 16 is 0); sketches are carried along the join
- * with OR as counts are with +.  sketches: device, a_domain x 16 uint32,
- * overwritten (sketch of a at [16 a, 16 a + 16)).  estimates: device,
+ * with OR as counts are with +.  sketches: device, 16-byte aligned,
+ * a_domain x 16 uint32, overwritten (sketch of a at [16 a, 16 a + 16)); a
+ * misaligned pointer is MWJ_ERR_INVALID_ARG.  estimates: device,
  * a_domain floats, or NULL: (16 / 0.77351) * 2^(mean over bitmaps of the
  * index of their lowest 0 bit).  Every a of R must lie in [0, a_domain)
  * (MWJ_ERR_DOMAIN from mwj_stream_status otherwise).  shares: s[0] = H(B)

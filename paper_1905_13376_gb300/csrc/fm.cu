@@ -17,8 +17,8 @@
 //
 // R and S are partitioned by H(B) as in Algorithm 1; bucket i's on-chip table
 // holds S_i's B values with their 64-byte sketches (the "~100 bytes per
-// tuple" of the paper's footnote).  A half-warp handles one tuple, one
-// bitmap per lane.  The estimate of |D(a)| is (M / PHI) * 2^(mean R_j),
+// tuple" of the paper's footnote).  Four lanes handle one tuple, four
+// bitmaps (16 bytes) per lane.  The estimate of |D(a)| is (M / PHI) * 2^(mean R_j),
 // R_j the lowest 0 bit of bitmap j, PHI = 0.77351.
 #include "api_internal.h"
 #include "tables.h"
@@ -50,32 +50,39 @@ __device__ __forceinline__ void fm_bit(int32_t d, uint32_t *j, uint32_t *r) {
     *r = q ? (uint32_t)(__ffs((int)q) - 1) : 27u;
 }
 
-// slot of c in T's packed key table (-1 if absent)
-__device__ __forceinline__ int64_t tkey_slot(const unsigned long long *tbl, uint32_t mask, uint32_t seed,
-                                             uint32_t c) {
+constexpr uint32_t kNoIndex = 0xFFFFFFFFu;
+
+// dense sketch index of c from T's key table, whose entries hold
+// (index << 32 | c) once k_fm_index has run (kNoIndex if c is absent)
+__device__ __forceinline__ uint32_t tkey_index(const unsigned long long *tbl, uint32_t mask, uint32_t seed,
+                                               uint32_t c) {
     uint32_t s = slot_of(c, seed, mask);
     for (uint32_t it = 0; it <= mask; ++it) {
         const unsigned long long x = __ldg(tbl + s);
-        if (x == kEmpty64) return -1;
-        if ((uint32_t)x == c) return s;
+        if (x == kEmpty64) return kNoIndex;
+        if ((uint32_t)x == c) return (uint32_t)(x >> 32);
         s = (s + 1) & mask;
     }
-    return -1;
+    return kNoIndex;
 }
 
 // dense index of every occupied slot of T's key table (warp-aggregated
-// counter; the order of the indices is immaterial); count = their number
-__global__ void k_fm_index(const unsigned long long *__restrict__ tbl, const uint32_t *__restrict__ meta,
-                           uint32_t *__restrict__ idx, unsigned int *__restrict__ count) {
+// counter; the order of the indices is immaterial), stored in the entry's
+// upper half in place of the degree; count = their number.  An index is
+// below 2^31, so an entry never becomes kEmpty64.
+__global__ void k_fm_index(unsigned long long *__restrict__ tbl, const uint32_t *__restrict__ meta,
+                           unsigned int *__restrict__ count) {
     const uint64_t slots = (uint64_t)meta[0] + 1;
     for (uint64_t s0 = (uint64_t)blockIdx.x * blockDim.x; s0 < slots; s0 += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = s0 + threadIdx.x;
-        const bool occ = s < slots && tbl[s] != kEmpty64;
+        const unsigned long long x = s < slots ? tbl[s] : kEmpty64;
+        const bool occ = x != kEmpty64;
         const unsigned m = __ballot_sync(0xffffffffu, occ);
         unsigned base = 0;
         if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(count, (unsigned)__popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (occ) idx[s] = base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+        const unsigned idx = base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+        if (occ) tbl[s] = ((unsigned long long)idx << 32) | (uint32_t)x;
     }
 }
 
@@ -91,7 +98,7 @@ __global__ void k_fm_zero(uint32_t *__restrict__ sk, const unsigned int *__restr
 __global__ void __launch_bounds__(256) k_fm_tsketch(const int32_t *__restrict__ tc, const int32_t *__restrict__ td,
                                                     uint32_t n, const unsigned long long *__restrict__ tbl,
                                                     const uint32_t *__restrict__ meta, uint32_t seed,
-                                                    const uint32_t *__restrict__ idx, uint32_t *__restrict__ skT) {
+                                                    uint32_t *__restrict__ skT) {
     const uint32_t mask = __ldg(meta);
     constexpr uint32_t K = 8;
     for (uint32_t i = (blockIdx.x * 256 + threadIdx.x) * K; i < n; i += gridDim.x * 256 * K) {
@@ -101,9 +108,9 @@ __global__ void __launch_bounds__(256) k_fm_tsketch(const int32_t *__restrict__ 
         for (uint32_t j = 0; j < FM_M; ++j) loc[j] = 0;
         int32_t cur = __ldg(tc + i);
         auto flush = [&](int32_t c) {
-            const int64_t s = tkey_slot(tbl, mask, seed, (uint32_t)c);
-            if (s < 0) return;   // cannot happen: every c of T is in the table
-            uint32_t *dst = skT + (size_t)__ldg(idx + s) * FM_M;
+            const uint32_t ix = tkey_index(tbl, mask, seed, (uint32_t)c);
+            if (ix == kNoIndex) return;   // cannot happen: every c of T is in the table
+            uint32_t *dst = skT + (size_t)ix * FM_M;
 #pragma unroll
             for (uint32_t j = 0; j < FM_M; ++j)
                 if (loc[j]) atomicOr(dst + j, loc[j]);
@@ -129,10 +136,9 @@ __global__ void __launch_bounds__(256) k_fm_tsketch(const int32_t *__restrict__ 
 struct FmArgs {
     const uint2 *Rp, *Sp;
     const uint32_t *offR, *offS;
-    const unsigned long long *ttbl;   // T's key table (packed, single)
+    const unsigned long long *ttbl;   // T's key table, entries (dense index << 32 | c)
     const uint32_t *tmeta;
     uint32_t tseed;
-    const uint32_t *tidx;             // dense index per slot
     const uint32_t *skT;              // dense sketches of T's keys
     uint32_t seed_slot;
     int32_t a_domain;
@@ -153,11 +159,20 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
     const uint32_t r0 = g.offR[i], r1 = g.offR[i + 1], s0 = g.offS[i], s1 = g.offS[i + 1];
     if (r0 >= r1 || s0 >= s1) return;
     const uint32_t tmask = __ldg(g.tmeta);
-    const uint32_t l16 = threadIdx.x & 15, half = threadIdx.x >> 4, halves = FT / 16;
+    // four lanes per tuple, bitmaps 4 l4 .. 4 l4 + 3 on lane l4
+    const uint32_t l4 = threadIdx.x & 3, grp = threadIdx.x >> 2, groups = FT / 4;
 
-    auto tsk = [&](int32_t c) -> uint32_t {   // word l16 of skT(c) (0 if c not in T)
-        const int64_t s = tkey_slot(g.ttbl, tmask, g.tseed, (uint32_t)c);
-        return s < 0 ? 0u : __ldg(g.skT + (size_t)__ldg(g.tidx + s) * FM_M + l16);
+    auto tsk = [&](int32_t c) -> uint4 {   // this lane's bitmaps of skT(c) (0 if c not in T)
+        const uint32_t ix = tkey_index(g.ttbl, tmask, g.tseed, (uint32_t)c);
+        return ix == kNoIndex ? make_uint4(0u, 0u, 0u, 0u)
+                              : __ldg((const uint4 *)(g.skT + (size_t)ix * FM_M) + l4);
+    };
+    auto or_in = [&](int slot, const uint4 &v) {   // w(b) |= skT(c), this lane's 4 bitmaps
+        uint32_t *dst = w + (uint32_t)slot * FM_M + 4 * l4;
+        if (v.x) atomicOr(dst, v.x);
+        if (v.y) atomicOr(dst + 1, v.y);
+        if (v.z) atomicOr(dst + 2, v.z);
+        if (v.w) atomicOr(dst + 3, v.w);
     };
     auto clear = [&]() {   // ends with a barrier
         for (uint32_t s = threadIdx.x; s <= cap; s += FT) keys[s] = kEmptyKey;
@@ -175,10 +190,10 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
         uint32_t cend = s1;
         bool ok = false;
         if (pos == s0) {
-            // optimistic pass: one tuple per half-warp; its 16 lanes insert the
-            // same key (idempotent: the first CAS wins) and OR one bitmap each
+            // optimistic pass: one tuple per four lanes; they insert the same
+            // key (idempotent: the first CAS wins) and OR four bitmaps each
             uint32_t fresh_n = 0;
-            for (uint32_t t = s0 + half; t < s1; t += halves) {
+            for (uint32_t t = s0 + grp; t < s1; t += groups) {
                 if (*(volatile uint32_t *)&bad) break;
                 const uint2 st = __ldg(g.Sp + t);
                 bool fresh;
@@ -188,8 +203,7 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
                     atomicOr(&bad, 1u);
                     break;
                 }
-                const uint32_t v = tsk((int32_t)st.y);
-                if (v) atomicOr(&w[(uint32_t)slot * FM_M + l16], v);
+                or_in(slot, tsk((int32_t)st.y));
             }
             fresh_n = warp_sum(fresh_n);
             if ((threadIdx.x & 31) == 0 && fresh_n) atomicAdd(&nd, fresh_n);
@@ -200,7 +214,7 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
         }
         if (!ok) {
             // bounded rounds of at most cap / 4 tuples while the table stays at
-            // most 3/4 full; one tuple per half-warp again
+            // most 3/4 full; one tuple per four lanes again
             const uint32_t rt = cap / 4;
             cend = pos;
             for (;;) {
@@ -210,17 +224,16 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
                 if (cend >= s1 || filled + rt > cap - cap / 4) break;
                 const uint32_t e = min(s1, cend + rt);
                 uint32_t fresh_n = 0;
-                for (uint32_t t = cend + half; t < e; t += halves) {
+                for (uint32_t t = cend + grp; t < e; t += groups) {
                     const uint2 st = __ldg(g.Sp + t);
                     bool fresh;
                     const int slot = tbl_insert(keys, mask, st.x, g.seed_slot, &fresh);
                     fresh_n += fresh;
                     if (slot < 0) {   // cannot happen: the table is never full
-                        if (l16 == 0) set_status(g.st, MWJ_ERR_CHECK, 9);
+                        if (l4 == 0) set_status(g.st, MWJ_ERR_CHECK, 9);
                         continue;
                     }
-                    const uint32_t v = tsk((int32_t)st.y);
-                    if (v) atomicOr(&w[(uint32_t)slot * FM_M + l16], v);
+                    or_in(slot, tsk((int32_t)st.y));
                 }
                 fresh_n = warp_sum(fresh_n);
                 if ((threadIdx.x & 31) == 0 && fresh_n) atomicAdd(&nd, fresh_n);
@@ -228,15 +241,19 @@ __global__ void __launch_bounds__(FT) k_fm_probe(FmArgs g) {
             }
         }
         // R_i streams past: sk(a) |= w(b), only bits that are new cost an atomic
-        for (uint32_t t = r0 + half; t < r1; t += halves) {
+        for (uint32_t t = r0 + grp; t < r1; t += groups) {
             const uint2 tr = __ldg(g.Rp + t);
             if ((uint32_t)tr.x >= (uint32_t)g.a_domain) continue;   // reported by the partitioner
             const int slot = tbl_find(keys, mask, tr.y, g.seed_slot);
             if (slot < 0) continue;
-            const uint32_t v = w[(uint32_t)slot * FM_M + l16];
-            if (!v) continue;
-            uint32_t *dst = g.out + (size_t)tr.x * FM_M + l16;
-            if (v & ~__ldcg(dst)) atomicOr(dst, v);
+            const uint4 v = *(const uint4 *)(w + (uint32_t)slot * FM_M + 4 * l4);
+            if (!(v.x | v.y | v.z | v.w)) continue;
+            uint32_t *dst = g.out + (size_t)tr.x * FM_M + 4 * l4;
+            const uint4 cur = __ldcg((const uint4 *)dst);
+            if (v.x & ~cur.x) atomicOr(dst, v.x);
+            if (v.y & ~cur.y) atomicOr(dst + 1, v.y);
+            if (v.z & ~cur.z) atomicOr(dst + 2, v.z);
+            if (v.w & ~cur.w) atomicOr(dst + 3, v.w);
         }
         __syncthreads();   // the table is rebuilt for the next chunk
         pos = cend;
@@ -261,7 +278,6 @@ struct FmLayout {
     uint64_t *ttbl;
     uint32_t *tmeta;
     unsigned int *hll;
-    uint32_t *tidx;
     unsigned int *tcount;
     uint32_t *skT;
     void *pscratch;
@@ -277,7 +293,6 @@ size_t fm_layout(Arena &A, uint32_t I, const mwj_rel &R, const mwj_rel &S, const
     L.ttbl = A.take<uint64_t>(single_table_slots(T.n));
     L.tmeta = A.take<uint32_t>(4);
     L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
-    L.tidx = A.take<uint32_t>(single_table_slots(T.n));
     L.tcount = A.take<unsigned int>(4);
     L.skT = A.take<uint32_t>((size_t)(T.n + 1) * FM_M);
     size_t ps = part_scratch_bytes(R.n, I, num_sms);
@@ -326,7 +341,7 @@ extern "C" mwj_status mwj_fm_workspace_size(mwj_ctx *ctx, mwj_rel R, mwj_rel S, 
 extern "C" mwj_status mwj_fm_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T, const mwj_shares *shares,
                                     int32_t a_domain, uint32_t *sketches, float *estimates, void *workspace,
                                     size_t ws_bytes, void *stream) {
-    if (!ctx || !sketches || a_domain <= 0) return MWJ_ERR_INVALID_ARG;
+    if (!ctx || !sketches || a_domain <= 0 || ((uintptr_t)sketches & 15)) return MWJ_ERR_INVALID_ARG;
     ApiScope api_scope(&ctx->prof);
     if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
     uint32_t I;
@@ -352,7 +367,7 @@ extern "C" mwj_status mwj_fm_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel 
         return cuda_fail(ctx, e, "T keys");
     {
         ProfScope ps_("fm_index", st);
-        k_fm_index<<<sms * 4, 256, 0, st>>>((const unsigned long long *)L.ttbl, L.tmeta, L.tidx, L.tcount);
+        k_fm_index<<<sms * 4, 256, 0, st>>>((unsigned long long *)L.ttbl, L.tmeta, L.tcount);
     }
     {
         ProfScope ps_("fm_zero", st);
@@ -363,7 +378,7 @@ extern "C" mwj_status mwj_fm_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel 
         const uint64_t groups = ((uint64_t)T.n + 8 * 256 - 1) / (8 * 256);
         const unsigned grid = (unsigned)(groups < (uint64_t)sms * 8 ? groups : (uint64_t)sms * 8);
         k_fm_tsketch<<<grid, 256, 0, st>>>(T.x, T.y, (uint32_t)T.n, (const unsigned long long *)L.ttbl, L.tmeta,
-                                          sd.slot2, L.tidx, L.skT);
+                                          sd.slot2, L.skT);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "T sketches");
     // R and S by H(B) (Algorithm 1's first level)
@@ -383,7 +398,6 @@ extern "C" mwj_status mwj_fm_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel 
     g.ttbl = (const unsigned long long *)L.ttbl;
     g.tmeta = L.tmeta;
     g.tseed = sd.slot2;
-    g.tidx = L.tidx;
     g.skT = L.skT;
     g.seed_slot = sd.slot;
     g.a_domain = a_domain;

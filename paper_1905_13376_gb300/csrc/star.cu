@@ -330,7 +330,7 @@ struct StarPlan {
 struct StarLayout {
     uint64_t *tblR, *tblT;          // aggregates: single tables
     uint32_t *metaR, *metaT;
-    unsigned int *hll;
+    unsigned int *hll, *hllT;       // separate scratch: the two tables are built concurrently
     uint2 *Rp, *Tp;
     uint32_t *offR, *offT;
     uint64_t *imgR, *imgT;
@@ -383,6 +383,7 @@ size_t star_layout(Arena &A, const StarPlan &p, const mwj_rel &R, const mwj_rel 
         L.tblT = A.take<uint64_t>(single_table_slots(T.n));
         L.metaT = A.take<uint32_t>(4);
         L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
+        L.hllT = A.take<unsigned int>(hll_scratch_registers(num_sms));
         L.w = p.group ? A.take<unsigned long long>(single_table_slots(R.n)) : nullptr;
         L.Rp = L.Tp = nullptr;
         L.offR = L.offT = L.capR = L.capT = L.startR = L.startT = nullptr;
@@ -395,7 +396,7 @@ size_t star_layout(Arena &A, const StarPlan &p, const mwj_rel &R, const mwj_rel 
     }
     L.tblR = L.tblT = nullptr;
     L.metaR = L.metaT = nullptr;
-    L.hll = nullptr;
+    L.hll = L.hllT = nullptr;
     L.w = nullptr;
     L.Rp = A.take<uint2>(R.n + 2);
     L.offR = A.take<uint32_t>(p.JR + 1);
@@ -470,14 +471,33 @@ extern "C" mwj_status mwj_join3_star(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel
         (e = cudaMemsetAsync(out->group_counts, 0, sizeof(int64_t) * (size_t)out->a_domain, st)) !=
             cudaSuccess)
         return cuda_fail(ctx, e, "memset group_counts");
+    // the caller's stream waits for the side stream on every return after
+    // the fork, so no work of this call outlives it
+    struct JoinGuard {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        bool armed;
+        ~JoinGuard() {
+            if (armed) cudaStreamWaitEvent(st, ev, 0);
+        }
+    } join_guard{st, ctx->join, false};
     if (!p.rows) {
-        // the aggregates: one degree table per dimension relation
+        // the aggregates: one degree table per dimension relation, T's on the
+        // side stream while R's is built here
+        if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "fork");
+        e = single_table_direct(T.x, T.n, sd.slot2, L.hllT, L.metaT, L.tblT, single_table_slots(T.n),
+                                ctx->status, sms, ctx->side);
+        const cudaError_t ej = cudaEventRecord(ctx->join, ctx->side);
+        if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
+        join_guard.armed = true;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "T table");
         if ((e = single_table_direct(R.y, R.n, sd.slot, L.hll, L.metaR, L.tblR, single_table_slots(R.n),
                                      ctx->status, sms, st)) != cudaSuccess)
             return cuda_fail(ctx, e, "R table");
-        if ((e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.metaT, L.tblT, single_table_slots(T.n),
-                                     ctx->status, sms, st)) != cudaSuccess)
-            return cuda_fail(ctx, e, "T table");
+        if ((e = cudaStreamWaitEvent(st, ctx->join, 0)) != cudaSuccess) return cuda_fail(ctx, e, "join");
+        join_guard.armed = false;
         if (p.group &&
             (e = cudaMemsetAsync(L.w, 0, sizeof(unsigned long long) * single_table_slots(R.n), st)) !=
                 cudaSuccess)
