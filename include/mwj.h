@@ -125,10 +125,18 @@ mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_
 
 /* Linear 3-way join R(A,B) S(B,C) T(C,D) in one step (Algorithm 1, Section 4):
  * R is partitioned by H(B), S by (H(B), g(C)), T by g(C); each CTA holds one
- * R bucket as an on-chip hash table while the matching S partition streams
- * past it and T's bucket tables are probed (in shared memory when
- * shares.s[1] > 1, in L2 when shares.s[1] == 1).  No intermediate relation
- * is materialised.  workspace: device, >= mwj_workspace_size(ctx, MWJ_LINEAR, ...). */
+ * H(B) bucket's B values as an on-chip hash table while the other side of
+ * that bucket streams past it, and T's tables are probed (its bucket images
+ * when shares.s[1] > 1, one L2-resident table when shares.s[1] == 1).  For
+ * MATERIALIZE the table holds R's bucket (Algorithm 1's roles); for COUNT and
+ * GROUP BY A it holds S's bucket with w(b) = sum of deg_T(c) whenever
+ * |S| <= 2 |R| (each R tuple is then read once), else R's.  For COUNT and
+ * GROUP BY A, B keys heavy enough to unbalance the buckets (sampled) are
+ * routed to one extra bucket that every CTA aggregates.  No intermediate
+ * relation is materialised.  The call may run parts of its work on the
+ * context's own streams; they are joined back to `stream` before it returns
+ * (also on errors).  workspace: device, >= mwj_workspace_size(ctx,
+ * MWJ_LINEAR, ...). */
 mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
                             const mwj_shares *shares, const mwj_out *out,
                             void *workspace, size_t ws_bytes, void *stream);
