@@ -8,7 +8,10 @@
  *   cyclic  R(A,B) |x| S(B,C) |x| T(C,A)   (Section 5)
  *
  * and the cascade of two binary hash joins the paper measures them against
- * (Section 6.3).  Results follow bag semantics (duplicates are not removed,
+ * (Section 6.3); the star variant of the linear join (Section 6), the chain
+ * of four relations and Flajolet-Martin sketches of the friends-of-friends-
+ * of-friends query (Sections 4.1 and 7); a batched mode and a learned
+ * planner.  Results follow bag semantics (duplicates are not removed,
  * Section 1, Example 1) and are exact: counts are 64-bit and wrap modulo 2^64.
  *
  * Conventions shared by every entry point
@@ -108,8 +111,10 @@ typedef struct {
 typedef struct mwj_ctx mwj_ctx;
 
 /* Create a context on cfg->device (or the current device when cfg == NULL or
- * device == -1).  Allocates the context's device status word.  Returns
- * MWJ_ERR_CUDA if no usable sm_103 device is present. */
+ * device == -1).  Allocates the context's device status word and creates two
+ * internal streams and their events (work a join call forks onto them is
+ * joined back to the caller's stream within the call).  Returns MWJ_ERR_CUDA
+ * if no usable sm_103 device is present. */
 mwj_status mwj_create(mwj_ctx **ctx, const mwj_config *cfg);
 mwj_status mwj_destroy(mwj_ctx *ctx);
 
