@@ -202,7 +202,8 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     launches = ctx.launch_count() - launches0
     # per-kernel times: the same steps again with an event pair around every
-    # launch (outside the timed region above)
+    # launch (outside the timed region above; the library runs them on one
+    # stream while profiling, so each kernel is timed alone)
     ctx.set_profiling(True)
     ctx.reset_phase_times()
     for _ in range(args.steps):

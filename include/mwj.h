@@ -278,7 +278,11 @@ const char *mwj_last_error(mwj_ctx *ctx);
  * counterpart in the paper (its numbers come from a performance model).
  * mwj_set_profiling(ctx, 1) makes every kernel the context launches record a
  * CUDA event pair on its stream (a pool of 2^15 launches; later launches are
- * counted but not timed until mwj_reset_phase_times).  mwj_launch_count
+ * counted but not timed until mwj_reset_phase_times); while it is on, work a
+ * call would overlap on the context's internal streams runs on the caller's
+ * stream instead, so that each event pair times its kernel alone (the
+ * results are the same; the call's total time is then that of the
+ * serialised kernels).  mwj_launch_count
  * returns the number of kernels the context has launched since it was
  * created, whether or not profiling is on.  mwj_get_phase_times synchronises
  * on the recorded events and fills up to `max` entries of per-kernel-name

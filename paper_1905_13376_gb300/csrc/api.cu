@@ -379,13 +379,17 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
             if (armed) cudaStreamWaitEvent(st, ev, 0);
         }
     } join_guard{st, ctx->join, false}, join_guard2{st, ctx->join2, false};
+    // with per-kernel profiling on, everything runs on the caller's stream so
+    // that each kernel's event pair times that kernel alone
+    cudaStream_t side = ctx->prof.on ? st : ctx->side;
+    cudaStream_t side2 = ctx->prof.on ? st : ctx->side2;
     if (p.single) {
         if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(side, ctx->fork, 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "fork");
         e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
-                                ctx->status, ctx->dev.num_sms, ctx->side);
-        const cudaError_t ej = cudaEventRecord(ctx->join, ctx->side);   // whatever was queued
+                                ctx->status, ctx->dev.num_sms, side);
+        const cudaError_t ej = cudaEventRecord(ctx->join, side);   // whatever was queued
         if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
         join_guard.armed = true;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "T tables");
@@ -409,11 +413,11 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     if (out->mode == MWJ_COUNT_GROUP_BY_A) pr.dom = (uint32_t)out->a_domain;   // every a of R in the domain
     if (p.single) {
         if ((e = cudaEventRecord(ctx->heavy_ready, st)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ctx->side2, ctx->heavy_ready, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(side2, ctx->heavy_ready, 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "fork");
         e = part_run(R.x, R.y, R.n, pr, PAY_PAIR, L.Rp, L.offR, L.pscratchR, L.pscratch_bytes,
-                     ctx->dev.num_sms, ctx->side2);
-        const cudaError_t ej = cudaEventRecord(ctx->join2, ctx->side2);
+                     ctx->dev.num_sms, side2);
+        const cudaError_t ej = cudaEventRecord(ctx->join2, side2);
         if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
         join_guard2.armed = true;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "partition R");

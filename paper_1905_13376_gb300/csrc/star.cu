@@ -484,12 +484,14 @@ extern "C" mwj_status mwj_join3_star(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel
     if (!p.rows) {
         // the aggregates: one degree table per dimension relation, T's on the
         // side stream while R's is built here
+        // (with per-kernel profiling on, on the caller's stream: see the linear join)
+        cudaStream_t side = ctx->prof.on ? st : ctx->side;
         if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(side, ctx->fork, 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "fork");
         e = single_table_direct(T.x, T.n, sd.slot2, L.hllT, L.metaT, L.tblT, single_table_slots(T.n),
-                                ctx->status, sms, ctx->side);
-        const cudaError_t ej = cudaEventRecord(ctx->join, ctx->side);
+                                ctx->status, sms, side);
+        const cudaError_t ej = cudaEventRecord(ctx->join, side);
         if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
         join_guard.armed = true;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "T table");
