@@ -33,7 +33,17 @@ UNIT = "tuples/s"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # kernels from one ncu capture, valid only for the library sources they were
 # taken from (digest of csrc/ + include/).  Filled from profiles/.
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from
+# one ncu capture, per step of the benchmark workload, valid while the sources
+# the kernel is built from are unchanged (digest of those files).  The
+# scatter's capture ran on the 2^19-vertex graph (16,090,397 edges: S's and R's
+# scatter moved 215.5 + 260.6 MB) and is scaled by the edge count to the
+# 2^20-vertex graph (32,804,288 edges, x 2.0387): traffic grows with the tuples
+# partitioned (the bucket count is the same).
+TRAFFIC = {
+    "part_scatter": {"bytes_per_step": 970_700_000, "digest": "a8955b800db65c70",
+                     "sources": ["csrc/partition.cu", "csrc/common.cuh", "csrc/internal.h", "csrc/skew.h"]},
+}
 
 
 def peaks():
@@ -100,13 +110,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def lib_digest():
+def source_digest(names):
+    """sha256 prefix of the named library sources (paths under the package)."""
     import hashlib
-    import glob
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1905_13376_gb300", "csrc", "*")) +
-                    [os.path.join(ROOT, "include", "mwj.h")]):
-        h.update(open(f, "rb").read())
+    for name in names:
+        path = os.path.join(ROOT, "paper_1905_13376_gb300", name)
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -304,7 +316,8 @@ def run_ours(args, rank, world, local_rank):
         if ab is not None:
             achieved = ab / (per_step[dom] * 1e-3) / 1e9
             tr = TRAFFIC.get(dom)
-            traffic = tr["bytes_per_step"] if tr and tr.get("digest") == lib_digest() else None
+            traffic = (tr["bytes_per_step"] if tr and tr.get("digest") == source_digest(tr["sources"])
+                       else None)
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "traffic": traffic, "peak_kind": peak_kind,
