@@ -84,7 +84,7 @@ typedef struct {
  *   cyclic: s = {H(A), G(B), F(C)} bucket counts; tile (i,j,k) joins
  *           R_ij, S_jk and T_ki.
  * Every used entry must be >= 1.  A NULL share pointer asks the library's
- * cost-model planner to choose. */
+ * cost-model planner to choose (mwj_plan_shares). */
 typedef struct {
     int32_t s[3];
 } mwj_shares;
@@ -128,8 +128,15 @@ mwj_status mwj_destroy(mwj_ctx *ctx);
 mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
                               const mwj_shares *shares, mwj_mode mode, size_t *bytes);
 
-/* Linear 3-way join R(A,B) S(B,C) T(C,D) in one step (Algorithm 1, Section 4):
- * R is partitioned by H(B), S by (H(B), g(C)), T by g(C); each CTA holds one
+/* Linear 3-way join R(A,B) S(B,C) T(C,D) in one step (Algorithm 1, Section 4).
+ * Shares s[0] = s[1] = 1 with COUNT or GROUP BY A (the default for those
+ * modes when shares == NULL): one bucket per side, nothing partitioned, the
+ * held tables kept whole in the L2: T's table c -> deg_T(c) is built (on a
+ * context stream) while S's weight table b -> w(b) is sized, a pass over S
+ * adds w(b) += deg_T(c), and a pass over R adds cnt[a] += w(b) and
+ * total += w(b).  Both tables are sized from HyperLogLog estimates of the
+ * distinct keys; w(b) is exact to 2^64.
+ * Otherwise R is partitioned by H(B), S by (H(B), g(C)), T by g(C); each CTA holds one
  * H(B) bucket's B values as an on-chip hash table while the other side of
  * that bucket streams past it, and T's tables are probed (its bucket images
  * when shares.s[1] > 1, one L2-resident table when shares.s[1] == 1).  For
@@ -265,7 +272,9 @@ mwj_status mwj_batch_launch(mwj_batch *batch, int64_t *counts, void *workspace, 
 mwj_status mwj_batch_destroy(mwj_batch *batch);
 
 /* The shares the planner would choose for these relations (host result in
- * *shares).  kind = MWJ_LINEAR, MWJ_CYCLIC or MWJ_STAR.  Synchronises
+ * *shares), the ones a call with shares == NULL uses.  kind = MWJ_LINEAR,
+ * MWJ_CYCLIC or MWJ_STAR.  Linear: {1, 1, 1} for COUNT and GROUP BY A (the
+ * one-bucket plan), H(B) buckets from |R| for MATERIALIZE.  Synchronises
  * `stream`. */
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
                            mwj_mode mode, mwj_shares *shares, void *stream);

@@ -6,6 +6,7 @@
 
 #include "api_internal.h"
 #include "linear.h"
+#include "linear_l2.h"
 #include "tables.h"
 #include "skew.h"
 
@@ -66,6 +67,7 @@ struct LinPlan {
     bool rows;
     bool single;   // T in one L2-resident table (S not split by C, count modes)
     bool heavy;    // aggregates: heavy B keys split off into one extra bucket
+    bool l2;       // aggregates with I = J = 1: S's weight table and T's table in the L2
 };
 
 // bucket count of T's tables: small buckets so that each is aggregated in
@@ -89,10 +91,25 @@ struct LinLayout {
     void *pscratch; size_t pscratch_bytes;
     void *pscratchR;   // single mode: R's own partition scratch (R is partitioned on the side stream)
     unsigned long long *rowcount, *base; void *sscratch;
+    WTable w; unsigned int *whll;   // one-bucket plan: S's weight table
 };
 
 size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S,
                   const mwj_rel &T, int num_sms, LinLayout &L) {
+    L = LinLayout{};
+    if (p.l2) {   // nothing is partitioned: T's table and S's weight table
+        L.img = A.take<uint64_t>(single_table_slots(T.n));
+        L.meta = A.take<uint32_t>(4);
+        L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
+        const size_t ws = w_table_slots(S.n) + 2;
+        L.w.W = A.take<unsigned long long>(ws);
+        L.w.hi = A.take<uint32_t>(ws);
+        L.w.meta = A.take<uint32_t>(4);
+        L.whll = A.take<unsigned int>(hll_scratch_registers(num_sms));
+        L.heavy = A.take<uint32_t>(kHeavyTableWords);
+        L.hw = A.take<unsigned long long>(kHeavySlots);
+        return A.used;
+    }
     const uint32_t extra = p.heavy ? 1u : 0u;   // the heavy-key bucket
     L.heavy = p.heavy ? A.take<uint32_t>(kHeavyTableWords) : nullptr;
     L.hw = p.heavy ? A.take<unsigned long long>(kHeavySlots) : nullptr;
@@ -163,6 +180,19 @@ mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S,
     uint32_t I = pow2_at_least(want);
     if (I > 16384) I = 16384;
     sh->s[0] = (int32_t)I;
+    sh->s[1] = 1;
+    sh->s[2] = 1;
+    return MWJ_OK;
+}
+
+// Default shares of mwj_join3_linear.  Aggregates: I = J = 1, the plan in
+// which S's weight table and T's table are held whole in the L2 and nothing
+// is partitioned.  Rows: the partitioned plan above (the row output needs the
+// a-lists of R's buckets in shared memory).
+mwj_status linear_default_shares(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                                 mwj_mode mode, mwj_shares *sh) {
+    if (mode == MWJ_MATERIALIZE) return plan_linear_default(ctx, R, S, T, sh);
+    sh->s[0] = 1;
     sh->s[1] = 1;
     sh->s[2] = 1;
     return MWJ_OK;
@@ -314,13 +344,14 @@ mwj_status mwj_workspace_size(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_
     if (mode < MWJ_COUNT || mode > MWJ_MATERIALIZE) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad mode");
     mwj_shares sh;
     if (kind == MWJ_LINEAR) {
-        if (shares) sh = *shares; else plan_linear_default(ctx, R, S, T, &sh);
+        if (shares) sh = *shares; else linear_default_shares(ctx, R, S, T, mode, &sh);
         LinPlan p;
         mwj_status s = lin_check_shares(ctx, &sh, &p.I, &p.J);
         if (s != MWJ_OK) return s;
         p.rows = (mode == MWJ_MATERIALIZE);
         p.single = (p.J == 1 && !p.rows);
         p.heavy = !p.rows;
+        p.l2 = (p.I == 1 && p.J == 1 && !p.rows);
         p.JT = t_buckets(T.n, p.J, p.single);
         Arena A(nullptr, 0);
         LinLayout L;
@@ -344,13 +375,14 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     if (s != MWJ_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     mwj_shares sh;
-    if (shares) sh = *shares; else plan_linear_default(ctx, R, S, T, &sh);
+    if (shares) sh = *shares; else linear_default_shares(ctx, R, S, T, out->mode, &sh);
     LinPlan p;
     s = lin_check_shares(ctx, &sh, &p.I, &p.J);
     if (s != MWJ_OK) return s;
     p.rows = (out->mode == MWJ_MATERIALIZE);
     p.single = (p.J == 1 && !p.rows);
     p.heavy = !p.rows;
+    p.l2 = (p.I == 1 && p.J == 1 && !p.rows);
     p.JT = t_buckets(T.n, p.J, p.single);
     Arena A(workspace, ws_bytes);
     LinLayout L;
@@ -383,6 +415,36 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     // that each kernel's event pair times that kernel alone
     cudaStream_t side = ctx->prof.on ? st : ctx->side;
     cudaStream_t side2 = ctx->prof.on ? st : ctx->side2;
+    if (p.l2) {
+        // T's table on the side stream while S's weight table is sized and
+        // cleared here; then the S pass and the R pass
+        if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(side, ctx->fork, 0)) != cudaSuccess)
+            return cuda_fail(ctx, e, "fork");
+        e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
+                                ctx->status, ctx->dev.num_sms, side);
+        const cudaError_t ej = cudaEventRecord(ctx->join, side);
+        if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
+        join_guard.armed = true;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "T table");
+        L.w.seed = sd.slot;
+        L.w.heavy = L.heavy;
+        if ((e = heavy_detect(R.y, R.n, S.x, S.n, kWHeavyBuckets, L.heavy, L.hw, st)) != cudaSuccess)
+            return cuda_fail(ctx, e, "heavy keys");
+        e = w_table_prepare(S.x, S.n, L.w, L.whll, w_table_slots(S.n), ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "S weight table");
+        e = cudaStreamWaitEvent(st, ctx->join, 0);
+        join_guard.armed = false;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "join");
+        const TImg t{L.img, nullptr, nullptr, nullptr, nullptr, L.meta, 0u, sd.C, sd.slot2};
+        e = w_table_build(S.x, S.y, S.n, t, L.w, ctx->status, ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "S pass");
+        const int mode = out->mode == MWJ_COUNT_GROUP_BY_A ? 1 : 0;
+        e = w_table_probe(R.x, R.y, R.n, L.w, mode, out->a_domain, (unsigned long long *)out->group_counts,
+                          (unsigned long long *)out->total, ctx->status, ctx->dev.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "R pass");
+        return MWJ_OK;
+    }
     if (p.single) {
         if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(side, ctx->fork, 0)) != cudaSuccess)
@@ -480,11 +542,10 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
 
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, mwj_mode mode,
                            mwj_shares *shares, void *stream) {
-    (void)mode;
     (void)stream;
     if (!ctx || !shares) return MWJ_ERR_INVALID_ARG;
     if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
-    if (kind == MWJ_LINEAR) return plan_linear_default(ctx, R, S, T, shares);
+    if (kind == MWJ_LINEAR) return linear_default_shares(ctx, R, S, T, mode, shares);
     if (kind == MWJ_CYCLIC) return plan_cyclic_default(ctx, R, S, T, shares);
     if (kind == MWJ_STAR) return plan_star_default(R, T, shares);
     return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind");

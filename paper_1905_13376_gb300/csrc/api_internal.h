@@ -35,6 +35,8 @@ mwj_status check_out(mwj_ctx *ctx, const mwj_out *out, int arity);
 
 mwj_status plan_linear_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
                                mwj_shares *sh);
+mwj_status linear_default_shares(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                                 mwj_mode mode, mwj_shares *sh);
 mwj_status plan_cyclic_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
                                mwj_shares *sh);
 mwj_status cyc_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,

@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
 }  // namespace
 
 cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
-                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st) {
+                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st,
+                              const char *hll_name, const char *size_name) {
     cudaError_t e;
     const uint32_t nn = (uint32_t)n;
     const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
@@ -544,14 +545,14 @@ cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, uns
     unsigned int *done = tail + 3 * HLL_MCTAS;
     uint32_t rows = ctas;
     if (nn > 0) {
-        ProfScope ps_("t_hll", st);
+        ProfScope ps_(hll_name, st);
         k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs, done);
     } else {
         rows = 1;
         if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(done, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     }
-    ProfScope ps_("t_size", st);
+    ProfScope ps_(size_name, st);
     k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor, meta);
     return cudaGetLastError();
 }

@@ -70,8 +70,10 @@ cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, u
                                 DevStatus *status, int num_sms, cudaStream_t st);
 // Only the sizing step of single_table_direct: meta[0] = mask of a table of
 // 2^k >= 4 x (estimated distinct keys) slots (at most reserve_slots).
+// hll_name, size_name: the two launches' names in the per-kernel profile.
 cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
-                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st);
+                              uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st,
+                              const char *hll_name = "t_hll", const char *size_name = "t_size");
 uint32_t hll_registers();
 size_t hll_scratch_registers(int num_sms);
 // HyperLogLog registers of keys[0, n) into regs[0, hll_registers()); regs must

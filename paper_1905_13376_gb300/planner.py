@@ -99,7 +99,10 @@ def features(ctx: binding.Context, kind, R, S, T) -> np.ndarray:
 
 
 def scaled_shares(ctx, kind, R, S, T, k: int):
-    base = ctx.plan_shares(kind, R, S, T)
+    # the scale applies to the partitioned plan (the library's default for
+    # row output); the one-bucket plan the linear aggregates default to is
+    # not in this family
+    base = ctx.plan_shares(kind, R, S, T, binding.MWJ_MATERIALIZE)
     if kind == binding.MWJ_LINEAR:
         I = max(1, min(16384, int(base[0] * 2.0 ** k)))
         return (I, 1, 1)

@@ -94,6 +94,7 @@ def test_many_distinct_keys_in_one_bucket_chunks(ctx):
     S = (g.integers(0, n, n).astype(np.int32), g.integers(0, 3000, n).astype(np.int32))
     T = (g.integers(0, 3000, n).astype(np.int32), g.integers(0, 10, n).astype(np.int32))
     check_all_modes(ctx, R, S, T, 1000, shares=(1, 1))
+    check_all_modes(ctx, R, S, T, 1000, shares=(2, 1))
     check_all_modes(ctx, R, S, T, 1000, shares=(2, 3))
 
 
@@ -146,19 +147,28 @@ def test_aliased_self_join(ctx):
     assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
 
 
+def partitioned(ctx, R, S, T):
+    """The library's partitioned plan (its default for row output)."""
+    return ctx.plan_shares(binding.MWJ_LINEAR, R, S, T, binding.MWJ_MATERIALIZE)
+
+
 def test_uniform_config_full_size(ctx):
     R, S, T = datagen.linear_uniform()
     check_all_modes(ctx, R, S, T, 1 << 20, rows=False)
+    dR = cu(R)
+    check_all_modes(ctx, R, S, T, 1 << 20, shares=partitioned(ctx, dR, dR, dR), rows=False)
 
 
 def test_friends_workload_full_size(ctx):
     """F |x| F |x| F GROUP BY A on the 2^20-vertex power-law graph, the benchmark
-    workload, with the shares the library plans for it: every count exact."""
+    workload, with the default plan (one bucket per side) and the partitioned
+    plan: every count exact."""
     F = datagen.chung_lu_directed()
     dF = cu(F)
     want = oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=1 << 20)
-    got = ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=1 << 20)
-    assert int(got["total"].item()) == want["total"]
-    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
-    got = ctx.join3_linear(dF, dF, dF, "count")
-    assert int(got["total"].item()) == want["total"]
+    for shares in (None, partitioned(ctx, dF, dF, dF)):
+        got = ctx.join3_linear(dF, dF, dF, "group_by_a", shares=shares, a_domain=1 << 20)
+        assert int(got["total"].item()) == want["total"]
+        assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+        got = ctx.join3_linear(dF, dF, dF, "count", shares=shares)
+        assert int(got["total"].item()) == want["total"]

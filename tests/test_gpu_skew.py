@@ -33,7 +33,7 @@ def check(ctx, R, S, T, a_domain, shares=None):
 
 
 @pytest.mark.parametrize("s", [0.8, 1.1, 1.5, 2.0])
-@pytest.mark.parametrize("shares", [None, (64, 1), (16, 4), (1, 1)])
+@pytest.mark.parametrize("shares", [None, (64, 1), (16, 4), (1, 1), (1024, 1)])
 def test_zipf_join_column(ctx, s, shares):
     R, S, T = datagen.skewed_linear(n=1 << 15, s=s, b_domain=1 << 12, c_domain=1 << 10,
                                     a_domain=1 << 10, seed=int(10 * s))
@@ -50,6 +50,7 @@ def test_heavy_keys_only_in_one_relation(ctx):
          g.integers(0, 300, n).astype(np.int32))
     T = (g.integers(0, 300, n).astype(np.int32), g.integers(0, 100, n).astype(np.int32))
     check(ctx, R, S, T, 100)
+    check(ctx, R, S, T, 100, (64, 1))
     check(ctx, R, S, T, 100, (8, 2))
 
 
@@ -66,12 +67,15 @@ def test_many_heavy_keys(ctx):
 
 def test_skewed_full_size(ctx):
     """The skew workload of the benchmark line: 2^22 tuples per relation,
-    B Zipf(1.5) (the top key holds ~38% of R and of S)."""
+    B Zipf(1.5) (the top key holds ~38% of R and of S), with the default plan
+    (one bucket per side) and the partitioned plan with its heavy-key bucket."""
     R, S, T = datagen.skewed_linear()
     total, cnt = factorised_group_by(R, S, T, 1 << 20)
     dR, dS, dT = cu(R), cu(S), cu(T)
-    got = ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=1 << 20)
-    assert int(got["total"].item()) == total
-    assert np.array_equal(got["counts"].cpu().numpy(), cnt)
-    got = ctx.join3_linear(dR, dS, dT, "count")
-    assert int(got["total"].item()) == total
+    part = ctx.plan_shares(binding.MWJ_LINEAR, dR, dS, dT, binding.MWJ_MATERIALIZE)
+    for shares in (None, part):
+        got = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=shares, a_domain=1 << 20)
+        assert int(got["total"].item()) == total
+        assert np.array_equal(got["counts"].cpu().numpy(), cnt)
+        got = ctx.join3_linear(dR, dS, dT, "count", shares=shares)
+        assert int(got["total"].item()) == total
