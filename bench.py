@@ -30,9 +30,6 @@ if ROOT not in sys.path:
 METRIC = "3-way join input tuples/s + % HBM roofline, multiway vs cascade, exact counts"
 UNIT = "tuples/s"
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels from one ncu capture, valid only for the library sources they were
-# taken from (digest of csrc/ + include/).  Filled from profiles/.
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from
 # one ncu capture, per step of the benchmark workload, valid while the sources
 # the kernel is built from are unchanged (digest of those files).  The
@@ -40,9 +37,15 @@ UNIT = "tuples/s"
 # scatter moved 215.5 + 260.6 MB) and is scaled by the edge count to the
 # 2^20-vertex graph (32,804,288 edges, x 2.0387): traffic grows with the tuples
 # partitioned (the bucket count is the same).
+# The one-bucket S pass (w_build) was captured the same way on the 2^19-vertex
+# graph (162.3 MB read + 5.0 MB written) and scaled by the same factor (its
+# tables double with the vertex count as well).
 TRAFFIC = {
     "part_scatter": {"bytes_per_step": 970_700_000, "digest": "a8955b800db65c70",
                      "sources": ["csrc/partition.cu", "csrc/common.cuh", "csrc/internal.h", "csrc/skew.h"]},
+    "w_build": {"bytes_per_step": 341_100_000, "digest": "9b0107d39de13914",
+                "sources": ["csrc/linear_l2.cu", "csrc/linear_l2.h", "csrc/common.cuh", "csrc/internal.h",
+                            "csrc/skew.h", "csrc/tables.h"]},
 }
 
 
@@ -131,8 +134,18 @@ def make_workload(args):
     return F, desc
 
 
-def algorithmic_bytes(name, nR, nS, nT, a_domain, tslots, launches):
+def algorithmic_bytes(name, nR, nS, nT, a_domain, tslots, launches, wslots=0):
     """Bytes a kernel must move per step (each buffer once at its stored size)."""
+    if name == "w_build":
+        # S streamed once (8 B per tuple); T's table read and S's weight
+        # table written once, both at their stored size
+        return 8 * nS + 8 * tslots + 8 * wslots
+    if name == "w_probe_groupby":
+        return 8 * nR + 8 * wslots + 8 * a_domain
+    if name == "w_probe_count":
+        return 8 * nR + 8 * wslots
+    if name == "t_insert":
+        return 4 * nT + 8 * tslots
     if name == "lin_probe_groupby":
         return 8 * nR + 8 * nS + 8 * tslots + 8 * a_domain
     if name == "lin_probe_count":
@@ -146,6 +159,23 @@ def algorithmic_bytes(name, nR, nS, nT, a_domain, tslots, launches):
     if name == "t_aggregate":
         return 4 * nT + 8 * nT
     return None
+
+
+def timed_ms(fn, stream, steps, warm=3):
+    """Mean CUDA-event milliseconds of fn() over `steps` calls on `stream`,
+    after `warm` untimed calls."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
 
 
 def max_over_ranks(values, device):
@@ -290,6 +320,20 @@ def run_ours(args, rank, world, local_rank):
                 "intermediate_rows": nI, "intermediate_bytes": 12 * nI, "steps": csteps,
                 "multiway_speedup": cms / ms, "exact_match": True}
 
+    # the partitioned plan on the same workload: R and S by H(B) into
+    # shared-memory buckets (Algorithm 1 with the library's default bucket
+    # count for row output)
+    part = None
+    if not args.no_partitioned and rank == 0:
+        psh = ctx.plan_shares(binding.MWJ_LINEAR, dF, dF, dF, binding.MWJ_MATERIALIZE)
+        rp = ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain)
+        pexact = int(rp["total"].item()) == total and torch.equal(rp["counts"], r["counts"])
+        pms = timed_ms(lambda: ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain,
+                                                sync=False), stream, args.steps)
+        part = {"impl": "partitioned: R and S by H(B), each bucket's B values in shared memory",
+                "shares": list(psh), "value": 3 * n / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms,
+                "default_plan_speedup": pms / ms, "exact_match": bool(pexact)}
+
     star = None if args.no_star or rank != 0 else run_star(ctx, stream, args, peaks())
     skew = None if args.no_skew or rank != 0 else run_skew(ctx, stream, args)
     join4 = None if args.no_join4 or rank != 0 else run_join4(ctx, stream, args, F)
@@ -302,17 +346,19 @@ def run_ours(args, rank, world, local_rank):
     tuples = 3 * n
     value = replica_throughput(tuples, world, ms)
     peak, peak_kind = peaks()
-    # T's single table: 2^k >= 4 x (estimated distinct C values) slots of 8 bytes
+    # T's single table and S's weight table: 2^k >= 4 x (estimated distinct
+    # keys) slots of 8 bytes; both are keyed by F's source column here
     dc = int(np.count_nonzero(np.bincount(F[0], minlength=a_domain)))
     tslots = 16
     while tslots < 4 * dc:
         tslots *= 2
+    wslots = tslots
     # dominant kernel and its roofline
     per_step = {k: v[0] / args.steps for k, v in phases.items()}
     dom = max(per_step, key=per_step.get) if per_step else None
     roof = None
     if dom:
-        ab = algorithmic_bytes(dom, n, n, n, a_domain, tslots, phases[dom][1] / args.steps)
+        ab = algorithmic_bytes(dom, n, n, n, a_domain, tslots, phases[dom][1] / args.steps, wslots)
         if ab is not None:
             achieved = ab / (per_step[dom] * 1e-3) / 1e9
             tr = TRAFFIC.get(dom)
@@ -329,15 +375,19 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded power-law graph)",
-        "config": {"workload": desc, "impl": "multiway (single-step 3-way hash join)",
+        "config": {"workload": desc,
+                   "impl": ("multiway (single-step 3-way hash join)" +
+                            (", one bucket per side: T's table and S's weight table held in L2"
+                             if tuple(shares[:2]) == (1, 1) else ", partitioned")),
                    "shares": list(shares), "tuples_per_step": tuples, "result_total": total,
                    "result_tuples_per_s": total * world / (ms * 1e-3),
-                   "l2": "inputs (268 MB) and partitions exceed the 129 MB L2; no flush",
+                   "l2": "every input column pair (262 MB) exceeds the 129 MB L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof, "kernels": kernels,
         "e2e": {"value": replica_throughput(tuples, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
-        "gpu_launches": launches, "clocks": clocks, "cascade": casc, "star": star, "skew": skew,
+        "gpu_launches": launches, "clocks": clocks, "partitioned": part, "cascade": casc, "star": star,
+        "skew": skew,
         "join4": join4, "fm": fmr,
     }
     return out, F
@@ -405,13 +455,14 @@ def run_star(ctx, stream, args, pk):
 
 
 def run_skew(ctx, stream, args):
-    """The linear GROUP BY A with a Zipf(1.5) join column shared by R and S
-    (heavy keys split off into their own bucket), checked exactly against
-    the factorised sum cnt(a) = sum over (a,b) in R of sum over (b,c) in S of
+    """The linear GROUP BY A with a Zipf(1.5) join column shared by R and S,
+    with the default plan (heavy keys summed per CTA) and the partitioned one
+    (heavy keys split off into their own bucket), checked exactly against the
+    factorised sum cnt(a) = sum over (a,b) in R of sum over (b,c) in S of
     deg_T(c)."""
     import numpy as np
     import torch
-    from paper_1905_13376_gb300 import datagen
+    from paper_1905_13376_gb300 import binding, datagen
 
     R, S, T = datagen.skewed_linear()
     n = len(R[0])
@@ -431,24 +482,24 @@ def run_skew(ctx, stream, args):
     wR = np.where(kb[p] == R[1].astype(np.int64) + off, w[p], 0)
     want = np.zeros(adom, dtype=np.int64)
     np.add.at(want, R[0].astype(np.int64), wR)
-    r = ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom)
-    exact = int(r["total"].item()) == int(want.sum()) and np.array_equal(r["counts"].cpu().numpy(), want)
-    for _ in range(3):
-        ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom, sync=False)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom, sync=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    psh = ctx.plan_shares(binding.MWJ_LINEAR, dR, dS, dT, binding.MWJ_MATERIALIZE)
+    exact = True
+    for sh in (None, psh):
+        r = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=sh, a_domain=adom)
+        exact = exact and int(r["total"].item()) == int(want.sum()) and \
+            np.array_equal(r["counts"].cpu().numpy(), want)
+    ms = timed_ms(lambda: ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom, sync=False),
+                  stream, args.steps)
+    pms = timed_ms(lambda: ctx.join3_linear(dR, dS, dT, "group_by_a", shares=psh, a_domain=adom,
+                                            sync=False), stream, args.steps)
     top = float(np.bincount(S[0]).max()) / n
     return {"workload": f"linear R|x|S|x|T GROUP BY A, {n} tuples per relation, B Zipf(1.5) in R and S "
                         f"(one key map; top key {top:.1%} of S), A, C, D uniform",
+            "impl": "one bucket per side; heavy keys summed per CTA in shared memory",
             "value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "exact_match": bool(exact),
-            "result_total": int(want.sum())}
+            "result_total": int(want.sum()),
+            "partitioned": {"impl": "partitioned by H(B) with the heavy keys in one extra bucket",
+                            "shares": list(psh), "ms_per_step": pms, "value": 3 * n / (pms * 1e-3)}}
 
 
 def run_join4(ctx, stream, args, F):
@@ -552,6 +603,8 @@ def main():
                     help="I J [log2 table slots]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-partitioned", action="store_true",
+                    help="skip timing the partitioned plan beside the default one")
     ap.add_argument("--no-fm", action="store_true",
                     help="skip the Flajolet-Martin sketch arm")
     ap.add_argument("--no-join4", action="store_true",
