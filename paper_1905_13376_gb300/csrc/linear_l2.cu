@@ -43,8 +43,8 @@ __device__ __forceinline__ void warp_runs(const int32_t (&k)[WQ], const unsigned
                                           uint32_t m, F &&emit) {
     const uint32_t lane = threadIdx.x & 31;
     const bool has = m > 0;
-    // the lane's first run (kf, sf) and last run (kl, sl); runs between them
-    // end inside the lane
+    // the lane's first run (kf, sf) and last run (kl, run); runs between
+    // them end inside the lane and are emitted here
     int32_t kf = k[0], kl = k[0];
     unsigned long long sf = 0, run = 0;
     uint32_t nruns = 0;
