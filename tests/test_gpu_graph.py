@@ -1,6 +1,7 @@
 """A linear-join call captured into a CUDA graph: the work the call forks onto
-the context's side streams (T's table, R's partition) is captured through the
-event fork/join and replays to the oracle's result."""
+the context's side streams (T's table, and with partitions R's partition) is
+captured through the event fork/join and replays to the oracle's result, with
+the default plan (one bucket per side) and a partitioned one."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,8 @@ from gpu_util import cu
 pytestmark = pytest.mark.gpu
 
 
-def test_linear_group_by_in_a_cuda_graph():
+@pytest.mark.parametrize("shares", [(64, 1), None])
+def test_linear_group_by_in_a_cuda_graph(shares):
     import torch
     torch.cuda.set_device(0)
     ctx = binding.Context(0)
@@ -23,11 +25,11 @@ def test_linear_group_by_in_a_cuda_graph():
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         # warm-up outside the capture: sizes the context's workspace
-        ctx.join3_linear(dR, dS, dT, "group_by_a", shares=(64, 1), a_domain=1 << 12, stream=s)
+        ctx.join3_linear(dR, dS, dT, "group_by_a", shares=shares, a_domain=1 << 12, stream=s)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        out = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=(64, 1), a_domain=1 << 12, stream=s,
+        out = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=shares, a_domain=1 << 12, stream=s,
                                sync=False)
     for _ in range(2):
         g.replay()
