@@ -303,6 +303,10 @@ class Context:
 
     def join3_linear(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
                      stream=None, sync=True):
+        """Linear 3-way join R(A,B) S(B,C) T(C,D).  shares = (H(B) buckets,
+        g(C) buckets[, log2 on-chip table slots]); None: one bucket per side
+        for "count" and "group_by_a" (T's and S's tables in L2), H(B)
+        buckets from |R| for "rows"."""
         return self._run(self.lib.mwj_join3_linear, MWJ_LINEAR, R, S, T, mode, shares, a_domain,
                          capacity, 4, stream, sync)
 
