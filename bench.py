@@ -57,10 +57,45 @@ def peaks():
     return 6800.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+def summarize_clocks(lines, t0=None, t1=None):
+    """Median SM clock, maximum SM clock and the slowdown reasons seen in
+    nvidia-smi sample lines (timestamp first, then ClockSampler.Q's fields).
+    With a window [t0, t1] (epoch seconds) only the samples taken inside it
+    count, when there are any; otherwise every sample does."""
+    import datetime
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    parsed = []
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            sm, mx = float(f[2]), float(f[3])
+        except ValueError:
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        active = [nm for k, nm in enumerate(names) if f[6 + k].lower().startswith("active")]
+        parsed.append((ts, sm, mx, active))
+    if not parsed:
+        return None
+    inside = [p for p in parsed if t0 is not None and p[0] is not None and t0 <= p[0] <= t1]
+    use = inside if inside else parsed
+    out = {"sm_mhz": statistics.median(p[1] for p in use), "sm_max_mhz": max(p[2] for p in use),
+           "reasons": sorted({r for p in use for r in p[3]}), "samples": len(use),
+           "in_timed_region": bool(inside)}
+    if t0 is not None:
+        out["window_ms"] = round((t1 - t0) * 1e3, 3)
+    return out
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons, one timestamped sample every
+    10 ms (as fast as nvidia-smi answers), kept for the timed region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -69,48 +104,36 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        """Start sampling; returns once the first sample is in (or after wait_s)."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + wait_s
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return None
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if f[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(list(self.lines), t0, t1)
 
 
 def source_digest(names):
@@ -232,15 +255,17 @@ def run_ours(args, rank, world, local_rank):
     clk.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()   # host window holding the timed region's device work
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    t1 = time.time()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    clocks = clk.stop(t0, t1)
     ms = e0.elapsed_time(e1) / args.steps
     launches = ctx.launch_count() - launches0
     # per-kernel times: the same steps again with an event pair around every
