@@ -235,8 +235,7 @@ __global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, 
                 }
             }
         }
-        warp_runs(b, x, m,
-                         [&](int32_t key, unsigned long long s) { w_add(w, wmask, (uint32_t)key, s, st); });
+        warp_runs(b, x, m, [&](int32_t key, unsigned long long s) { w_add(w, wmask, (uint32_t)key, s, st); });
 #pragma unroll
         for (int q = 0; q < WQ; ++q) {
             b[q] = nb[q];
@@ -308,7 +307,8 @@ __global__ void __launch_bounds__(WT) k_w_probe(const int32_t *__restrict__ Ra, 
         if (MODE == 1) {
 #pragma unroll
             for (int q = 0; q < WQ; ++q)
-                if ((uint32_t)q < m && (uint32_t)a[q] >= (uint32_t)a_domain) set_status(st, MWJ_ERR_DOMAIN, a[q]);
+                if ((uint32_t)q < m && (uint32_t)a[q] >= (uint32_t)a_domain)
+                    set_status(st, MWJ_ERR_DOMAIN, a[q]);
             warp_runs(a, x, m, [&](int32_t key, unsigned long long s) {
                 if ((uint32_t)key < (uint32_t)a_domain) atomicAdd(cnt + key, s);
             });
