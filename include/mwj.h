@@ -232,7 +232,9 @@ mwj_status mwj_cascade_join(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_re
  * Runs on the current device and `stream`, then synchronises `stream` and
  * returns any device-side error (e.g. MWJ_ERR_DOMAIN) directly.
  * The first call on a device looks up the scratch array's device address;
- * make it before any stream capture.  All calls share the one array: calls
+ * make it before any stream capture.  The address is kept for the life of
+ * the process: after cudaDeviceReset on a device the array lives at a new
+ * address, so the entry point must not be called on that device again.  All calls share the one array: calls
  * that overlap on the GPU (other streams, other host threads) race, so the
  * caller must serialise them.  Scratch that must start at zero is cleared by
  * every call. */

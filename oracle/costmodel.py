@@ -1,9 +1,9 @@
 """The paper's tuple-count cost analysis, written out -- TEST INFRASTRUCTURE ONLY.
 
-Each function restates one formula of the paper in its own notation; the
-library's share chooser and planner are checked against these.  M is the
-on-chip memory capacity in tuples, H, G, h, g the bucket counts of the hash
-functions of the same names (Section 3.1).
+Each function restates one formula of the paper in its own notation and is
+pinned by the tests to the numbers the paper prints (Examples 3 and 4) and to
+direct minimisation.  M is the on-chip memory capacity in tuples, H, G, h, g
+the bucket counts of the hash functions of the same names (Section 3.1).
 """
 from __future__ import annotations
 
@@ -50,7 +50,8 @@ def cyclic_crossover_M(nF: float, nI: float, factor: float = 2.0) -> float:
     """Example 4 with R = S = T = F: the M above which nF (1 + factor sqrt(nF/M)) < nI.
 
     factor = 2 is the optimal-H cost of Section 5.2; factor = 1 is the
-    expression Example 4 prints (see the readings of the paper's text).
+    expression Example 4 prints, which drops that factor 2 (its printed
+    crossover, about seven million tuples, follows from factor = 1).
     """
     root = (nI / nF - 1.0) / factor
     return nF / (root * root)
@@ -71,10 +72,3 @@ def branch_probability(g3: float, d: float) -> float:
     matches = nS * nT / d
     comparisons = nS * nT / g3
     return matches / comparisons
-
-
-def cascade_star_comparisons(nR: float, nS: float, nT: float, d: float,
-                             h: float, g: float) -> float:
-    """Section 6.5 (footnote): comparisons of the cascaded binary star join,
-    |R||S|/h + |R join S||T|/g with |R join S| = |R||S|/d."""
-    return nR * nS / h + nR * nS * nT / (d * g)

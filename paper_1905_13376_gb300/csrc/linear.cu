@@ -103,6 +103,10 @@ __device__ __forceinline__ int tbl_insert32(uint32_t *keys, uint32_t mask, uint3
 // Bulk-copy pipeline of two shared-memory buffers, each with a "full"
 // barrier: thread 0 refills a buffer after a CTA barrier has shown every
 // thread done with it.  Used to stage an R bucket tile into shared memory.
+// Polls a CTA spends, after a fill did not land within the context's wait
+// limit, waiting for its copies in flight before it returns.
+constexpr uint32_t kDrainLimit = 1u << 24;
+
 struct Ring {
     uint2 *buf;                     // 2 x RCH tuples
     unsigned long long *full;       // 2 barriers
@@ -138,11 +142,15 @@ __device__ __forceinline__ int build_all(const uint2 *__restrict__ Rp, uint32_t 
     }
     uint32_t fresh_n = 0;
     bool failed = false, late = false;
+    uint32_t late_c = 0;   // the chunk whose fill did not land in time
     for (uint32_t c = 0; c < nch; ++c) {
         const uint32_t b = c & 1u;
         late |= !mbar_wait_bounded(&ring.full[b], ring.uses[b] & 1u, spin_limit);
         ++ring.uses[b];
-        if (__syncthreads_or(late)) break;
+        if (__syncthreads_or(late)) {
+            late_c = c;
+            break;
+        }
         const uint32_t len = min(RCH, total - c * RCH);
         const uint32_t base = a0 + c * RCH;
         const uint2 *src = ring.buf + b * RCH;
@@ -163,9 +171,16 @@ __device__ __forceinline__ int build_all(const uint2 *__restrict__ Rp, uint32_t 
         if (threadIdx.x == 0 && c + 2 < nch) issue(c + 2);
     }
     if (late) {
-        // wait (bounded) for the fills still in flight before giving up
-        if (threadIdx.x == 0)
-            for (uint32_t b = 0; b < 2; ++b) mbar_wait_bounded(&ring.full[b], ring.uses[b] & 1u, spin_limit);
+        // Wait (bounded, with a fixed limit of its own) for the fills still
+        // in flight before the CTA lets go of its shared memory: the fill of
+        // chunk late_c, whose phase is the one before the increment above,
+        // and the fill of chunk late_c + 1 in the other buffer when it was
+        // issued (it was, before chunk late_c was waited on, if it exists).
+        if (threadIdx.x == 0) {
+            const uint32_t b = late_c & 1u;
+            mbar_wait_bounded(&ring.full[b], (ring.uses[b] - 1u) & 1u, kDrainLimit);
+            if (late_c + 1 < nch) mbar_wait_bounded(&ring.full[b ^ 1u], ring.uses[b ^ 1u] & 1u, kDrainLimit);
+        }
         __syncthreads();
         return -1;
     }

@@ -19,8 +19,11 @@
 // The first call on each device looks up the device addresses of the array
 // and of the status word (cudaGetSymbolAddress, with that device current);
 // make that first call before capturing the stream into a CUDA graph.  The
-// host never passes the array's name to a kernel: in host code that name is
-// a stand-in, not a device address.
+// addresses are kept until the process exits; cudaDeviceReset on a device
+// reloads the library's device image elsewhere, so the entry point must not
+// be called on that device after a reset.  The host never passes the
+// array's name to a kernel: in host code that name is a stand-in, not a
+// device address.
 #include <mutex>
 
 #include "api_internal.h"

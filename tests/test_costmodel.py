@@ -87,8 +87,21 @@ def test_branch_probability_and_intermediate():
     assert exact == pytest.approx(cm.intermediate_estimate(2e5, 2e5, d), rel=0.02)
 
 
-def test_star_comparisons_formula():
-    # the second term is |R join S||T|/g with |R join S| = |R||S|/d
-    nR, nS, nT, d, h, g = 1e3, 1e8, 2e3, 1e4, 64, 64
-    I = cm.intermediate_estimate(nR, nS, d)
-    assert cm.cascade_star_comparisons(nR, nS, nT, d, h, g) == pytest.approx(nR * nS / h + I * nT / g)
+def test_branch_probability_by_loop_nest():
+    """Appendix A's branch probability counted in the loop nest itself: S and T
+    with uniform C values in [0, d) hashed into g3 buckets (c mod g3); every
+    (s, t) pair of a bucket is one comparison, an equal pair is one match.
+    Over many draws matches / comparisons approaches g3 / d."""
+    rng = np.random.default_rng(3)
+    for g3, d in [(4, 64), (8, 40), (1, 10)]:
+        comps = matches = 0
+        for _ in range(200):
+            sc = rng.integers(0, d, 120)
+            tc = rng.integers(0, d, 90)
+            for k in range(g3):
+                sk, tk = sc[sc % g3 == k], tc[tc % g3 == k]
+                for s in sk:           # the nested loop of one bucket pair
+                    for t in tk:
+                        comps += 1
+                        matches += int(s == t)
+        assert matches / comps == pytest.approx(cm.branch_probability(g3, d), rel=0.05)

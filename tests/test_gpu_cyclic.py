@@ -130,9 +130,13 @@ def test_powerlaw_graph_medium(ctx):
 
 
 def test_triangle_workload_full_size_sampled(ctx):
-    """2^22-vertex power-law graph: GPU GROUP BY A, checked exactly on a sample
-    of A values (the oracle joined with R restricted to them), plus
-    sum(counts) == total == materialised row count."""
+    """2^22-vertex power-law graph (the triangle workload at full size): GPU
+    GROUP BY A checked exactly on a sample of A values (the oracle joined with
+    R restricted to them, the busiest A values included), sum(counts) ==
+    total == the COUNT mode's total == the materialised row count; the full
+    triangle list is materialised (capacity from the count) and its rows with
+    a sampled A, sorted, equal the oracle's rows for the restricted R."""
+    import torch
     a, b = datagen.chung_lu_undirected()
     R, S, T = datagen.triangle_relations(a, b)
     dR, dS, dT = cu(R), cu(S), cu(T)
@@ -140,6 +144,7 @@ def test_triangle_workload_full_size_sampled(ctx):
     got = ctx.join3_cyclic(dR, dS, dT, "group_by_a", a_domain=n_v)
     total = int(got["total"].item())
     counts = got["counts"].cpu().numpy()
+    del got
     assert int(counts.sum()) == total
     g = np.random.default_rng(1)
     hubs = np.argsort(-np.bincount(a))[:5].astype(np.int32)   # the busiest A values too
@@ -149,3 +154,16 @@ def test_triangle_workload_full_size_sampled(ctx):
     want = oracle.cyclic(Rs, S, T, oracle.GROUP_BY_A, a_domain=n_v)
     assert np.array_equal(counts[sample], want["counts"][sample])
     assert int(ctx.join3_cyclic(dR, dS, dT, "count")["total"].item()) == total
+    # the materialised list: exactly `total` rows, and the sampled A values'
+    # rows equal the oracle's
+    got = ctx.join3_cyclic(dR, dS, dT, "rows", capacity=total)
+    assert int(got["n_rows"].item()) == total
+    rows = got["rows"][:total]
+    assert rows.shape == (total, 3)
+    mask = torch.isin(rows[:, 0], torch.from_numpy(sample).to(rows.device))
+    mine = rows[mask].cpu().numpy()
+    # every row is a triangle a < b < c of the oriented graph (checked on the sample)
+    assert np.all(mine[:, 0] < mine[:, 1]) and np.all(mine[:, 1] < mine[:, 2])
+    del got, rows, mask
+    wr = oracle.cyclic(Rs, S, T, oracle.MATERIALIZE, capacity=int(want["total"]))
+    assert np.array_equal(sorted_rows(mine), wr["rows"])

@@ -172,3 +172,39 @@ def test_friends_workload_full_size(ctx):
         assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
         got = ctx.join3_linear(dF, dF, dF, "count", shares=shares)
         assert int(got["total"].item()) == want["total"]
+
+
+def test_bounded_wait_runs_out_then_context_recovers(ctx):
+    """A context whose device waits give up after one poll: the partitioned
+    plan with R's buckets on chip stages their tiles through bulk copies and
+    waits on the copies' barriers, so a call either lands every copy in time (the oracle's result)
+    or reports MWJ_ERR_TIMEOUT from the status word, each waiting CTA having
+    drained its copies in flight before it returned.  A following call on a
+    context with the default limit is exact."""
+    # |S| > 2|R| keeps R's buckets on chip (Algorithm 1's roles), whose tiles
+    # arrive by bulk copies
+    g = np.random.default_rng(31)
+    nR, nS, nT = 1 << 14, 3 << 14, 1 << 14
+    R = (g.integers(0, 1 << 10, nR).astype(np.int32), g.integers(0, 1 << 9, nR).astype(np.int32))
+    S = (g.integers(0, 1 << 9, nS).astype(np.int32), g.integers(0, 1 << 9, nS).astype(np.int32))
+    T = (g.integers(0, 1 << 9, nT).astype(np.int32), g.integers(0, 1 << 10, nT).astype(np.int32))
+    want = oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=1 << 10)
+    dR, dS, dT = cu(R), cu(S), cu(T)
+    impatient = binding.Context(0, spin_limit=1)
+    outcomes = set()
+    try:
+        for _ in range(3):
+            try:
+                got = impatient.join3_linear(dR, dS, dT, "group_by_a", shares=(64, 1, 1), a_domain=1 << 10)
+                assert int(got["total"].item()) == want["total"]
+                assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+                outcomes.add("ok")
+            except binding.MwjError as e:
+                assert e.status == binding.MWJ_ERR_TIMEOUT, e
+                outcomes.add("timeout")
+    finally:
+        impatient.close()
+    print("outcomes with a one-poll wait limit:", sorted(outcomes))
+    got = ctx.join3_linear(dR, dS, dT, "group_by_a", shares=(64, 1, 1), a_domain=1 << 10)
+    assert int(got["total"].item()) == want["total"]
+    assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])

@@ -45,3 +45,78 @@ def test_forward_shapes_and_layout():
     h1 = np.maximum(W["b1"], 0)
     h2 = np.maximum(h1 @ W["W2"] + W["b2"], 0)
     assert np.allclose(y, np.tile(h2 @ W["W3"] + W["b3"], (5, 1)))
+
+
+def _hand_network():
+    """A network whose output is worked out by hand: only a few weights are
+    non-zero, every value is exactly representable in BF16, and the entries
+    sit at asymmetric positions so that a transposed weight matrix, a swapped
+    layer, a missing or extra ReLU or a dropped bias changes the output."""
+    W = {name: np.zeros(shape) for name, shape in mlp.SIZES}
+    W["W1"][0, 5] = 1.0       # input 0 -> hidden-1 unit 5
+    W["W1"][1, 5] = 0.5       # input 1 -> hidden-1 unit 5
+    W["W1"][1, 9] = -1.0      # input 1 -> hidden-1 unit 9 (negative: cut by the ReLU)
+    W["b1"][9] = 0.25
+    W["b1"][17] = 2.0         # unit 17: bias only
+    W["W2"][5, 3] = 3.0       # hidden-1 unit 5 -> hidden-2 unit 3
+    W["W2"][17, 3] = -0.5
+    W["W2"][9, 40] = 7.0      # unit 9 is 0 after its ReLU, so unit 40 gets only its bias
+    W["b2"][40] = -1.0        # ... which is negative: unit 40 is cut as well
+    W["b2"][3] = 0.125
+    W["W2"][9, 50] = -2.0     # unit 50 sees unit 9 only after its ReLU (0 here, 7.5 without it)
+    W["W3"][3, 0] = 2.0
+    W["W3"][3, 2] = -1.0      # a negative output: no ReLU on the last layer
+    W["W3"][40, 1] = 100.0    # would show up if unit 40 survived
+    W["W3"][50, 0] = 1.0
+    W["b3"][:] = [0.5, -0.25, 1.0]
+    return np.concatenate([W[name].ravel() for name, _ in mlp.SIZES])
+
+
+def test_forward_hand_worked_network():
+    """x = (2, 4, 0, ...):
+    hidden 1: unit 5 = 1*2 + 0.5*4 = 4; unit 9 = relu(-4 + 0.25) = 0; unit 17 = 2.
+    hidden 2: unit 3 = 3*4 - 0.5*2 + 0.125 = 11.125; unit 40 = relu(7*0 - 1) = 0;
+    unit 50 = relu(-2*0) = 0.
+    output: (2*11.125 + 0.5, 0 - 0.25, -11.125 + 1) = (22.75, -0.25, -10.125)."""
+    p = _hand_network()
+    X = np.zeros((2, mlp.NIN))
+    X[0, 0], X[0, 1] = 2.0, 4.0
+    y = mlp.forward(p, X)[3]
+    assert np.array_equal(y[0], [22.75, -0.25, -10.125])
+    # zero input: hidden 1 unit 9 = 0.25, unit 17 = 2; hidden 2 unit 3 = -1 + 0.125 -> 0,
+    # unit 40 = relu(7*0.25 - 1) = 0.75, unit 50 = relu(-2*0.25) = 0;
+    # output = (0.5, 75 - 0.25, 1.0)
+    assert np.array_equal(y[1], [0.5, 74.75, 1.0])
+
+
+def test_forward_matches_per_neuron_loops():
+    """The definition neuron by neuron in plain Python floats (each sum in
+    float64, ReLU on the hidden layers only, BF16 rounding of inputs, weights
+    and hidden activations) against the vectorised oracle."""
+    g = np.random.default_rng(11)
+    p = mlp.init_params(12).astype(np.float64) + g.normal(0, 0.05, mlp.NPARAM)
+    X = g.normal(size=(3, mlp.NIN))
+    r = lambda v: float(mlp.bf16(np.float32(v))[()])
+    W = mlp.unpack(mlp.bf16(p))
+    want = np.zeros((3, mlp.NOUT))
+    for n in range(3):
+        x = [r(v) for v in X[n]]
+        h1 = []
+        for j in range(mlp.NH):
+            s = W["b1"][j]
+            for i in range(mlp.NIN):
+                s += x[i] * W["W1"][i, j]
+            h1.append(r(max(s, 0.0)))
+        h2 = []
+        for j in range(mlp.NH):
+            s = W["b2"][j]
+            for i in range(mlp.NH):
+                s += h1[i] * W["W2"][i, j]
+            h2.append(r(max(s, 0.0)))
+        for k in range(mlp.NOUT):
+            s = W["b3"][k]
+            for i in range(mlp.NH):
+                s += h2[i] * W["W3"][i, k]
+            want[n, k] = s
+    got = mlp.forward(p, X)[3]
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)

@@ -1,8 +1,9 @@
 """mwj_join3_linear_noalloc: the linear join for callers that cannot
 allocate device memory (it runs on a fixed scratch array inside the library
 instead of a context and a workspace).  Checked through the C ABI against
-mwj_join3_linear, the entry point that uses a caller workspace, on two calls
-in a row; exact integer equality is the tolerance of every join test here.
+mwj_join3_linear, the entry point that uses a caller workspace, and against
+the CPU oracle, on two calls in a row; exact integer equality is the
+tolerance of every join test here.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -11,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1905_13376_gb300 import binding, datagen
 
 from gpu_util import cu
@@ -52,12 +54,16 @@ def test_noalloc_matches_workspace_entry_point_twice():
         a_domain = int(max(R[0].max(), 0)) + 1
         dR, dS, dT = cu(R), cu(S), cu(T)
         ref = ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=a_domain)
+        want = oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=a_domain)
+        assert int(ref["total"].item()) == want["total"]
+        assert np.array_equal(ref["counts"].cpu().numpy(), want["counts"])
         for _ in range(2):   # two calls in a row share the scratch array
             st, total, cnt = _noalloc(lib, dR, dS, dT, binding.MWJ_COUNT_GROUP_BY_A, a_domain,
                                       stream)
             assert st == binding.MWJ_OK
             assert int(total.item()) == int(ref["total"].item())
             assert torch.equal(cnt, ref["counts"])
+            assert np.array_equal(cnt.cpu().numpy(), want["counts"])
             st, total, _ = _noalloc(lib, dR, dS, dT, binding.MWJ_COUNT, 0, stream)
             assert st == binding.MWJ_OK
             assert int(total.item()) == int(ref["total"].item())
