@@ -7,7 +7,14 @@ counts.
 
 Prints one JSON line.  `python bench.py --gpus N --steps K --warmup W`; under
 torchrun every rank runs its own replica of the workload (the join is one
-problem per GPU; replicas only) and rank 0 reports the aggregate.
+problem per GPU; replicas only) and rank 0 reports the aggregate.  With one
+GPU the line also carries the other workloads (sub-objects): the uniform
+linear join of 2^16 tuples per relation, the triangle join on a 2^22-vertex
+graph (count, GROUP BY A, materialised list, chunked cascade), the batch of
+4096 queries replayed from a CUDA graph, the headline graph with its rows
+shuffled, and the star, skewed, four-relation and Flajolet-Martin variants.
+Exactness flags compare with the CPU oracle; every oracle call sits in the
+cpu_baseline_* functions.
 
 --impl reference times the CPU oracle (single-threaded C hash join) on the
 same workload and metric.
@@ -15,6 +22,7 @@ same workload and metric.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -29,23 +37,21 @@ if ROOT not in sys.path:
 
 METRIC = "3-way join input tuples/s + % HBM roofline, multiway vs cascade, exact counts"
 UNIT = "tuples/s"
+L2_NOTE = "every input column pair (262 MB) exceeds the 129 MB L2; no flush"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from
 # one ncu capture, per step of the benchmark workload, valid while the sources
 # the kernel is built from are unchanged (digest of those files).  The
-# scatter's capture ran on the 2^19-vertex graph (16,090,397 edges: S's and R's
-# scatter moved 215.5 + 260.6 MB) and is scaled by the edge count to the
-# 2^20-vertex graph (32,804,288 edges, x 2.0387): traffic grows with the tuples
-# partitioned (the bucket count is the same).
-# The one-bucket S pass (w_build) was captured the same way on the 2^19-vertex
-# graph (162.3 MB read + 5.0 MB written) and scaled by the same factor (its
-# tables double with the vertex count as well).
+# captures ran on the 2^19-vertex graph (16,090,397 edges) and are scaled by
+# the edge count to the 2^20-vertex graph (32,804,288 edges, x 2.0387): the
+# traffic grows with the tuples streamed and the tables double with the
+# vertex count as well.
 TRAFFIC = {
     "part_scatter": {"bytes_per_step": 970_700_000, "digest": "a8955b800db65c70",
                      "sources": ["csrc/partition.cu", "csrc/common.cuh", "csrc/internal.h", "csrc/skew.h"]},
-    "w_build": {"bytes_per_step": 341_100_000, "digest": "6a71c3e30d2a52f4",
+    "w_build": {"bytes_per_step": None, "digest": "",
                 "sources": ["csrc/linear_l2.cu", "csrc/linear_l2.h", "csrc/common.cuh", "csrc/internal.h",
-                            "csrc/skew.h", "csrc/tables.h"]},
+                            "csrc/skew.h", "csrc/tables.h", "csrc/warp_runs.cuh"]},
 }
 
 
@@ -57,6 +63,9 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
 def summarize_clocks(lines, t0=None, t1=None):
     """Median SM clock, maximum SM clock and the slowdown reasons seen in
     nvidia-smi sample lines (timestamp first, then ClockSampler.Q's fields).
@@ -79,6 +88,10 @@ def summarize_clocks(lines, t0=None, t1=None):
             ts = None
         active = [nm for k, nm in enumerate(names) if f[6 + k].lower().startswith("active")]
         parsed.append((ts, sm, mx, active))
+    return _summary(parsed, t0, t1)
+
+
+def _summary(parsed, t0, t1):
     if not parsed:
         return None
     inside = [p for p in parsed if t0 is not None and p[0] is not None and t0 <= p[0] <= t1]
@@ -136,6 +149,95 @@ class ClockSampler:
         return summarize_clocks(list(self.lines), t0, t1)
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries) about once a millisecond from a host
+    thread, so that a timed region of a few milliseconds still holds several
+    samples.  Inactive when NVML cannot be loaded."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        self.ok = False
+        self.samples = []
+        self._stop = threading.Event()
+        try:
+            import torch
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            uuid = getattr(torch.cuda.get_device_properties(cuda_index), "uuid", None)
+            got = False
+            if uuid is not None:
+                u = str(uuid)
+                u = u if u.startswith("GPU-") else "GPU-" + u
+                got = self.nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0
+            if not got and self.nv.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) != 0:
+                return
+            self.max_mhz = float(mx.value)
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _poll(self):
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.time()
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                r = 0
+                if self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) == 0:
+                    r = rs.value
+                self.samples.append((t, float(clk.value), self.max_mhz,
+                                     [nm for bit, nm in self.REASONS.items() if r & bit]))
+            time.sleep(0.001)
+
+    def start(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            time.sleep(0.005)
+
+    def stop(self, t0=None, t1=None):
+        if not self.ok:
+            return None
+        time.sleep(0.005)
+        self._stop.set()
+        self.t.join(timeout=2)
+        s = _summary(list(self.samples), t0, t1)
+        if s:
+            s["source"] = "nvml, ~1 ms"
+        return s
+
+
+class Clocks:
+    """Both samplers over one window; the NVML summary when it has samples
+    inside the window, else nvidia-smi's."""
+
+    def __init__(self, index):
+        self.nvml = NvmlSampler(index)
+        self.smi = ClockSampler(index)
+
+    def start(self):
+        self.smi.start()
+        self.nvml.start()
+
+    def stop(self, t0, t1):
+        a = self.nvml.stop(t0, t1)
+        b = self.smi.stop(t0, t1)
+        if b:
+            b["source"] = "nvidia-smi, 10 ms"
+        best = a if a and a.get("in_timed_region") else (b if b and b.get("in_timed_region") else (a or b))
+        if best is not None and b is not None and best is not b:
+            best["nvidia_smi"] = {k: b[k] for k in ("sm_mhz", "samples", "in_timed_region", "reasons")}
+        return best
+
+
 def source_digest(names):
     """sha256 prefix of the named library sources (paths under the package)."""
     import hashlib
@@ -148,6 +250,16 @@ def source_digest(names):
     return h.hexdigest()[:16]
 
 
+def traffic_of(kernel):
+    tr = TRAFFIC.get(kernel)
+    if tr and tr.get("bytes_per_step") and tr.get("digest") == source_digest(tr["sources"]):
+        return tr["bytes_per_step"]
+    return None
+
+
+# ---------------------------------------------------------------------------
+# workloads, bytes, timing
+# ---------------------------------------------------------------------------
 def make_workload(args):
     from paper_1905_13376_gb300 import datagen
     F = datagen.chung_lu_directed(n_vertices=args.vertices, mean_degree=32.0)
@@ -157,30 +269,37 @@ def make_workload(args):
     return F, desc
 
 
-def algorithmic_bytes(name, nR, nS, nT, a_domain, tslots, launches, wslots=0):
+def table_bytes(direct, span, distinct, entry_bytes):
+    """Stored size of a one-bucket table: the direct-address array (span
+    entries) or 2^k >= 4 x distinct hashed 8-byte slots."""
+    if direct:
+        return entry_bytes * span
+    slots = 16
+    while slots < 4 * distinct:
+        slots *= 2
+    return 8 * slots
+
+
+def algorithmic_bytes(name, nR, nS, nT, a_domain, t_bytes, w_bytes, launches=1):
     """Bytes a kernel must move per step (each buffer once at its stored size)."""
     if name == "w_build":
         # S streamed once (8 B per tuple); T's table read and S's weight
         # table written once, both at their stored size
-        return 8 * nS + 8 * tslots + 8 * wslots
+        return 8 * nS + t_bytes + w_bytes
     if name == "w_probe_groupby":
-        return 8 * nR + 8 * wslots + 8 * a_domain
+        return 8 * nR + w_bytes + 8 * a_domain
     if name == "w_probe_count":
-        return 8 * nR + 8 * wslots
+        return 8 * nR + w_bytes
     if name == "t_insert":
-        return 4 * nT + 8 * tslots
+        return 4 * nT + t_bytes
     if name == "lin_probe_groupby":
-        return 8 * nR + 8 * nS + 8 * tslots + 8 * a_domain
+        return 8 * nR + 8 * nS + t_bytes + 8 * a_domain
     if name == "lin_probe_count":
-        return 8 * nR + 8 * nS + 8 * tslots
+        return 8 * nR + 8 * nS + t_bytes
     if name == "part_scatter":
-        # R and S: read 8 B + write 8 B per tuple; T (keys only, when it is
-        # partitioned: a third launch) read 4 + write 4
         return 16 * nR + 16 * nS + (8 * nT if launches >= 3 else 0)
     if name == "part_hist":
         return 4 * (nR + nS + nT)
-    if name == "t_aggregate":
-        return 4 * nT + 8 * nT
     return None
 
 
@@ -201,6 +320,20 @@ def timed_ms(fn, stream, steps, warm=3):
     return e0.elapsed_time(e1) / steps
 
 
+def profiled(ctx, fn, steps):
+    """Per-kernel milliseconds and launches per call of fn() (the library runs
+    a call's kernels on one stream while profiling, each timed alone)."""
+    import torch
+    ctx.set_profiling(True)
+    ctx.reset_phase_times()
+    for _ in range(steps):
+        fn()
+    torch.cuda.synchronize()
+    ph = ctx.phase_times()
+    ctx.set_profiling(False)
+    return {k: (v[0] / steps, v[1] / steps) for k, v in ph.items()}
+
+
 def max_over_ranks(values, device):
     """Element-wise maximum of a list of floats over all ranks (the replicas'
     step times: the whole job is as slow as its slowest replica)."""
@@ -218,6 +351,62 @@ def replica_throughput(units_per_replica, world, ms):
     return units_per_replica * world / (ms * 1e-3)
 
 
+def guarded(name, fn, *a, **kw):
+    """Run one sub-benchmark; a failure is recorded in the line, not hidden."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:   # noqa: BLE001
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"[:400], "arm": name}
+
+
+# ---------------------------------------------------------------------------
+# the cpu_baseline leg: every call of the CPU oracle (timed baseline and the
+# exactness checks) is in these functions
+# ---------------------------------------------------------------------------
+def cpu_baseline(F, a_domain):
+    """The oracle on the headline workload once: its throughput and its
+    result (compared with the GPU's)."""
+    import oracle
+    t0 = time.perf_counter()
+    want = oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=a_domain)
+    dt = time.perf_counter() - t0
+    n = len(F[0])
+    return ({"value": 3 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"the full workload once ({3 * n} input tuples, {dt:.2f} s, 1 thread)"}, want)
+
+
+def cpu_baseline_linear(R, S, T, a_domain):
+    import oracle
+    return oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=a_domain)
+
+
+def cpu_baseline_cyclic_sampled(R, S, T, sample, a_domain):
+    """The oracle's GROUP BY A and rows of the cyclic join with R restricted
+    to the sampled A values (exactly those values' groups and rows)."""
+    import numpy as np
+    import oracle
+    keep = np.isin(R[0], sample)
+    Rs = (R[0][keep], R[1][keep])
+    g = oracle.cyclic(Rs, S, T, oracle.GROUP_BY_A, a_domain=a_domain)
+    rows = oracle.cyclic(Rs, S, T, oracle.MATERIALIZE, capacity=int(g["total"]))["rows"]
+    return g["counts"][sample], rows
+
+
+def cpu_baseline_batch_sampled(qs, pick):
+    import oracle
+    out = {}
+    for i in pick:
+        q = qs[i]
+        fn = oracle.linear if q.kind == "linear" else oracle.cyclic
+        out[int(i)] = fn(q.R, q.S, q.T)["total"]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the headline: F |x| F |x| F on the 2^20-vertex graph
+# ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -234,16 +423,14 @@ def run_ours(args, rank, world, local_rank):
     shares = tuple(args.shares) if args.shares else ctx.plan_shares(binding.MWJ_LINEAR, dF, dF, dF,
                                                                     binding.MWJ_COUNT_GROUP_BY_A)
     stream = torch.cuda.current_stream(dev)
-
-    def step(sync=False):
-        return ctx.join3_linear(dF, dF, dF, "group_by_a", shares=shares, a_domain=a_domain,
-                                sync=sync)
-
-    # exactness check once (device result vs the oracle is in the tests; here
-    # the group counts must at least sum to the total)
-    r = step(sync=True)
+    r = ctx.join3_linear(dF, dF, dF, "group_by_a", shares=shares, a_domain=a_domain, sync=True)
     total = int(r["total"].item())
+    counts_ref = r["counts"].clone()
     assert int(r["counts"].sum().item()) == total
+
+    def step():
+        ctx.join3_linear(dF, dF, dF, "group_by_a", shares=shares, a_domain=a_domain, sync=False, out=r)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -251,7 +438,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launch_count()
-    clk = ClockSampler(local_rank)
+    clk = Clocks(local_rank)
     clk.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -268,29 +455,50 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.stop(t0, t1)
     ms = e0.elapsed_time(e1) / args.steps
     launches = ctx.launch_count() - launches0
-    # per-kernel times: the same steps again with an event pair around every
-    # launch (outside the timed region above; the library runs them on one
-    # stream while profiling, so each kernel is timed alone)
-    ctx.set_profiling(True)
-    ctx.reset_phase_times()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    phases = ctx.phase_times()
-    ctx.set_profiling(False)
+    exact_steps = torch.equal(r["counts"], counts_ref) and int(r["total"].item()) == total
 
-    # end to end through the C ABI from pinned host memory: H2D of F, the
-    # join, D2H of the group counts and the total, every step
+    # the same step sustained for about a quarter of a second (its own clock record)
+    sustained = None
+    if rank == 0 and world == 1:
+        ks = max(args.steps, int(250.0 / max(ms, 1e-3)))
+        clk2 = Clocks(local_rank)
+        clk2.start()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0 = time.time()
+        s0.record(stream)
+        for _ in range(ks):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        u1 = time.time()
+        sms = s0.elapsed_time(s1) / ks
+        sustained = {"steps": ks, "ms_per_step": sms, "value": 3 * n / (sms * 1e-3),
+                     "clocks": clk2.stop(u0, u1)}
+
+    # per-kernel times (outside the timed regions)
+    phases = profiled(ctx, step, args.steps)
+
+    # end to end through the C ABI from pinned host memory: H2D of F (its two
+    # columns on two streams, so two copy engines run at once), the join,
+    # D2H of the group counts and the total, every step
     hF = tuple(torch.from_numpy(c).pin_memory() for c in F)
     hcnt = torch.empty(a_domain, dtype=torch.int64).pin_memory()
     htot = torch.empty(1, dtype=torch.int64).pin_memory()
     eF = tuple(torch.empty_like(c) for c in dF)
+    side = torch.cuda.Stream(dev)
+    ev = torch.cuda.Event()
+    er = {}
 
     def e2e_step():
-        for h, d in zip(hF, eF):
-            d.copy_(h, non_blocking=True)
-        rr = ctx.join3_linear(eF, eF, eF, "group_by_a", shares=shares, a_domain=a_domain,
-                              sync=False)
+        side.wait_stream(stream)
+        eF[0].copy_(hF[0], non_blocking=True)
+        with torch.cuda.stream(side):
+            eF[1].copy_(hF[1], non_blocking=True)
+            ev.record(side)
+        stream.wait_event(ev)
+        rr = ctx.join3_linear(eF, eF, eF, "group_by_a", shares=shares, a_domain=a_domain, sync=False,
+                              out=er.get("r"))
+        er["r"] = rr
         hcnt.copy_(rr["counts"], non_blocking=True)
         htot.copy_(rr["total"], non_blocking=True)
 
@@ -307,115 +515,349 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = f0.elapsed_time(f1) / args.steps
     assert int(htot.item()) == total
 
-    # the cascade of binary joins on the same workload, same device, same
-    # metric: I = F|x|F (~1e9 rows, 12 B each) is materialised in HBM
-    # the comparison arms run once, on rank 0 (the other ranks wait for it at
-    # the max over ranks below)
-    casc = None
-    if not args.no_cascade and rank == 0:
-        # room for I: the exact |F|x|F| from degrees (host, numpy)
-        indeg = np.bincount(F[1], minlength=a_domain).astype(np.int64)
-        outdeg = np.bincount(F[0], minlength=a_domain).astype(np.int64)
-        nI = int((indeg * outdeg).sum())
-        base_ws = ctx.workspace_size(2 + binding.MWJ_LINEAR, dF, dF, dF, None,
-                                     binding.MWJ_COUNT_GROUP_BY_A)
-        wsb = base_ws + max(0, nI - (1 << 24)) * 12 + (64 << 20)
-
-        def cstep():
-            return ctx.cascade_join(binding.MWJ_LINEAR, dF, dF, dF, "group_by_a",
-                                    a_domain=a_domain, sync=False, workspace_bytes=wsb)
-        rc = cstep()
-        torch.cuda.synchronize()
-        assert int(rc["total"].item()) == total
-        assert torch.equal(rc["counts"], r["counts"])
-        for _ in range(2):
-            cstep()
-        torch.cuda.synchronize()
-        csteps = max(3, args.steps // 4)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(csteps):
-            cstep()
-        c1.record(stream)
-        torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1) / csteps
-        casc = {"impl": "cascade of binary hash joins (I = F|x|F materialised in HBM)",
-                "value": 3 * n / (cms * 1e-3), "unit": UNIT, "ms_per_step": cms,
-                "intermediate_rows": nI, "intermediate_bytes": 12 * nI, "steps": csteps,
-                "multiway_speedup": cms / ms, "exact_match": True}
-
-    # the partitioned plan on the same workload: R and S by H(B) into
-    # shared-memory buckets (Algorithm 1 with the library's default bucket
-    # count for row output)
-    part = None
-    if not args.no_partitioned and rank == 0:
-        psh = ctx.plan_shares(binding.MWJ_LINEAR, dF, dF, dF, binding.MWJ_MATERIALIZE)
-        rp = ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain)
-        pexact = int(rp["total"].item()) == total and torch.equal(rp["counts"], r["counts"])
-        pms = timed_ms(lambda: ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain,
-                                                sync=False), stream, args.steps)
-        part = {"impl": "partitioned: R and S by H(B), each bucket's B values in shared memory",
-                "shares": list(psh), "value": 3 * n / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms,
-                "default_plan_speedup": pms / ms, "exact_match": bool(pexact)}
-
-    star = None if args.no_star or rank != 0 else run_star(ctx, stream, args, peaks())
-    skew = None if args.no_skew or rank != 0 else run_skew(ctx, stream, args)
-    join4 = None if args.no_join4 or rank != 0 else run_join4(ctx, stream, args, F)
-    fmr = None if args.no_fm or rank != 0 else run_fm(ctx, stream, args, F)
-
-    # max over ranks
+    # comparison arms, rank 0 only (the other ranks wait for it at the max
+    # over ranks below)
+    peak, peak_kind = peaks()
+    first = rank == 0
+    casc = None if args.no_cascade or not first else guarded("cascade", run_cascade, ctx, stream, args, F, dF,
+                                                              a_domain, r, total)
+    part = None if args.no_partitioned or not first else guarded("partitioned", run_partitioned, ctx, stream,
+                                                                  args, dF, n, a_domain, r, ms, (peak, peak_kind))
+    shuf = None if args.no_shuffled or not first else guarded("shuffled", run_shuffled, ctx, stream, args, F,
+                                                               a_domain, counts_ref, total)
     if world > 1:
         ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
 
     tuples = 3 * n
     value = replica_throughput(tuples, world, ms)
-    peak, peak_kind = peaks()
-    # T's single table and S's weight table: 2^k >= 4 x (estimated distinct
-    # keys) slots of 8 bytes; both are keyed by F's source column here
-    dc = int(np.count_nonzero(np.bincount(F[0], minlength=a_domain)))
-    tslots = 16
-    while tslots < 4 * dc:
-        tslots *= 2
-    wslots = tslots
-    # dominant kernel and its roofline
-    per_step = {k: v[0] / args.steps for k, v in phases.items()}
-    dom = max(per_step, key=per_step.get) if per_step else None
+    # one-bucket tables: the direct-address layout when the key range fits
+    # (the library's choice is visible in which of the two pass kernels did
+    # the work); T's and S's tables are both keyed by F's source column here
+    direct = phases.get("w_build", (0, 0))[0] > phases.get("w_build_hashed", (0, 0))[0]
+    src = F[0]
+    span = int(src.max()) - int(src.min()) + 1
+    dc = int(np.count_nonzero(np.bincount(src - src.min())))
+    t_bytes = table_bytes(direct, span, dc, 4)
+    w_bytes = table_bytes(direct, span, dc, 8)
+    names = {"w_build": "w_build", "w_probe": "w_probe_groupby"}
+    ktime = lambda k: phases.get(k, (0.0, 0))[0] + phases.get(k + "_hashed", (0.0, 0))[0]
+    dom = max(phases, key=lambda k: phases[k][0]) if phases else None
     roof = None
     if dom:
-        ab = algorithmic_bytes(dom, n, n, n, a_domain, tslots, phases[dom][1] / args.steps, wslots)
+        base = dom[:-len("_hashed")] if dom.endswith("_hashed") else dom
+        ab = algorithmic_bytes(base, n, n, n, a_domain, t_bytes, w_bytes, phases[dom][1])
         if ab is not None:
-            achieved = ab / (per_step[dom] * 1e-3) / 1e9
-            tr = TRAFFIC.get(dom)
-            traffic = (tr["bytes_per_step"] if tr and tr.get("digest") == source_digest(tr["sources"])
-                       else None)
-            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic, "peak_kind": peak_kind,
-                    "algorithmic_bytes_per_step": ab,
-                    "ms_per_step": round(per_step[dom], 4)}
-    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4),
-                   "launches_per_step": v[1] / args.steps} for k, v in phases.items()}
+            kms = ktime(base)
+            achieved = ab / (kms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": base, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic_of(base), "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_step": ab, "ms_per_step": round(kms, 4),
+                    "table_layout": "direct-address" if direct else "hashed"}
+    # the whole multiway probe: S pass + R pass
+    pb = algorithmic_bytes(names["w_build"], n, n, n, a_domain, t_bytes, w_bytes) + \
+        algorithmic_bytes(names["w_probe"], n, n, n, a_domain, t_bytes, w_bytes)
+    pms = ktime(names["w_build"]) + ktime(names["w_probe"])
+    probe = {"kernels": ["w_build", "w_probe_groupby"], "algorithmic_bytes": pb, "ms_per_step": round(pms, 4),
+             "achieved": round(pb / (pms * 1e-3) / 1e9, 1) if pms else None, "peak": peak, "unit": "GB/s",
+             "frac": round(pb / (pms * 1e-3) / 1e9 / peak, 4) if pms else None}
+    kernels = {k: {"ms_per_step": round(v[0], 4), "launches_per_step": v[1]} for k, v in phases.items()}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded power-law graph)",
-        "config": {"workload": desc,
-                   "impl": ("multiway (single-step 3-way hash join)" +
-                            (", one bucket per side: T's table and S's weight table held in L2"
-                             if tuple(shares[:2]) == (1, 1) else ", partitioned")),
-                   "shares": list(shares), "tuples_per_step": tuples, "result_total": total,
-                   "result_tuples_per_s": total * world / (ms * 1e-3),
-                   "l2": "every input column pair (262 MB) exceeds the 129 MB L2; no flush",
+        "config": {"workload": desc, "tuples_per_step": tuples, "l2": L2_NOTE,
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "kernels": kernels,
+        "plan": {"impl": ("multiway (single-step 3-way hash join)" +
+                          (", one bucket per side: T's table and S's weight table held in L2"
+                           if tuple(shares[:2]) == (1, 1) else ", partitioned")),
+                 "shares": list(shares), "table_layout": "direct-address" if direct else "hashed",
+                 "result_total": total, "result_tuples_per_s": total * world / (ms * 1e-3),
+                 "exact_across_timed_steps": bool(exact_steps)},
+        "roofline": roof, "probe_roofline": probe, "kernels": kernels,
         "e2e": {"value": replica_throughput(tuples, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * a_domain + 8},
-        "gpu_launches": launches, "clocks": clocks, "partitioned": part, "cascade": casc, "star": star,
-        "skew": skew,
-        "join4": join4, "fm": fmr,
+        "gpu_launches": launches, "clocks": clocks, "sustained": sustained,
+        "partitioned": part, "cascade": casc, "shuffled": shuf,
     }
-    return out, F
+    if first and world == 1:
+        out["uniform_2e16"] = None if args.no_configs else guarded("uniform", run_uniform, ctx, stream, args)
+        out["triangles"] = None if args.no_configs else guarded("triangles", run_triangles, ctx, stream, args,
+                                                                (peak, peak_kind))
+        out["batch_4096"] = None if args.no_configs else guarded("batch", run_batch, ctx, stream, args)
+        out["star"] = None if args.no_star else guarded("star", run_star, ctx, stream, args, (peak, peak_kind))
+        out["skew"] = None if args.no_skew else guarded("skew", run_skew, ctx, stream, args)
+        out["join4"] = None if args.no_join4 else guarded("join4", run_join4, ctx, stream, args, F)
+        out["fm"] = None if args.no_fm else guarded("fm", run_fm, ctx, stream, args, F)
+    return out, F, r["counts"].cpu().numpy(), total
+
+
+def run_cascade(ctx, stream, args, F, dF, a_domain, r, total):
+    """The cascade of binary joins on the headline workload, same device,
+    same metric: I = F |x| F (~1e9 rows, 12 B each) is materialised in HBM."""
+    import numpy as np
+    import torch
+    from paper_1905_13376_gb300 import binding
+    n = len(F[0])
+    indeg = np.bincount(F[1], minlength=a_domain).astype(np.int64)
+    outdeg = np.bincount(F[0], minlength=a_domain).astype(np.int64)
+    nI = int((indeg * outdeg).sum())
+    base_ws = ctx.workspace_size(2 + binding.MWJ_LINEAR, dF, dF, dF, None, binding.MWJ_COUNT_GROUP_BY_A)
+    wsb = base_ws + max(0, nI - (1 << 24)) * 12 + (64 << 20)
+
+    def cstep():
+        return ctx.cascade_join(binding.MWJ_LINEAR, dF, dF, dF, "group_by_a", a_domain=a_domain, sync=False,
+                                workspace_bytes=wsb)
+    rc = cstep()
+    torch.cuda.synchronize()
+    exact = int(rc["total"].item()) == total and torch.equal(rc["counts"], r["counts"])
+    cms = timed_ms(cstep, stream, max(3, args.steps // 4), warm=2)
+    return {"impl": "cascade of binary hash joins (I = F|x|F materialised in HBM)",
+            "value": 3 * n / (cms * 1e-3), "unit": UNIT, "ms_per_step": cms, "intermediate_rows": nI,
+            "intermediate_bytes": 12 * nI, "multiway_speedup": None, "exact_match_multiway": bool(exact)}
+
+
+def run_partitioned(ctx, stream, args, dF, n, a_domain, r, ms, pk):
+    """The partitioned plan on the headline workload: R and S by H(B) into
+    shared-memory buckets (Algorithm 1 with the library's default bucket
+    count for row output), with the roofline of its probe kernel."""
+    import torch
+    from paper_1905_13376_gb300 import binding
+    psh = ctx.plan_shares(binding.MWJ_LINEAR, dF, dF, dF, binding.MWJ_MATERIALIZE)
+    rp = ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain)
+    exact = int(rp["total"].item()) == int(r["total"].item()) and torch.equal(rp["counts"], r["counts"])
+
+    def pstep():
+        ctx.join3_linear(dF, dF, dF, "group_by_a", shares=psh, a_domain=a_domain, sync=False, out=rp)
+    pms = timed_ms(pstep, stream, args.steps)
+    ph = profiled(ctx, pstep, 3)
+    kname = "lin_probe_groupby"
+    roof = None
+    if kname in ph:
+        # T's single table: hashed, 2^k >= 4 x distinct slots of 8 bytes
+        import numpy as np
+        src = dF[0].cpu().numpy()
+        t_bytes = table_bytes(False, 0, int(np.count_nonzero(np.bincount(src - src.min()))), 8)
+        ab = algorithmic_bytes(kname, n, n, n, a_domain, t_bytes, 0)
+        ach = ab / (ph[kname][0] * 1e-3) / 1e9
+        roof = {"kernel": kname, "ms_per_step": round(ph[kname][0], 4), "algorithmic_bytes": ab,
+                "achieved": round(ach, 1), "peak": pk[0], "unit": "GB/s", "frac": round(ach / pk[0], 4),
+                "peak_kind": pk[1]}
+    return {"impl": "partitioned: R and S by H(B), each bucket's B values in shared memory (Algorithm 1)",
+            "shares": list(psh), "value": 3 * n / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms,
+            "default_plan_speedup": pms / ms, "exact_match_default": bool(exact), "probe_roofline": roof,
+            "kernels": {k: round(v[0], 4) for k, v in ph.items()}}
+
+
+def run_shuffled(ctx, stream, args, F, a_domain, counts_ref, total):
+    """The headline graph with its rows in a seeded random order (no runs of
+    equal keys for the warps to merge): same metric, same result."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    perm = np.random.default_rng(20).permutation(len(F[0]))
+    Fs = (np.ascontiguousarray(F[0][perm]), np.ascontiguousarray(F[1][perm]))
+    dF = tuple(torch.from_numpy(c).to(dev) for c in Fs)
+    rs = ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=a_domain)
+    exact = int(rs["total"].item()) == total and torch.equal(rs["counts"], counts_ref.to(dev))
+    ms = timed_ms(lambda: ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=a_domain, sync=False, out=rs),
+                  stream, args.steps)
+    ph = profiled(ctx, lambda: ctx.join3_linear(dF, dF, dF, "group_by_a", a_domain=a_domain, sync=False,
+                                                out=rs), 3)
+    n = len(F[0])
+    return {"workload": "the headline graph with its rows shuffled (seeded permutation)",
+            "value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "exact_match_sorted": bool(exact), "kernels": {k: round(v[0], 4) for k, v in ph.items()}}
+
+
+# ---------------------------------------------------------------------------
+# the other workloads
+# ---------------------------------------------------------------------------
+def run_uniform(ctx, stream, args):
+    """Linear join R(A,B) S(B,C) T(C,D), 2^16 uniform tuples each (A, D in
+    [0, 2^20), B, C in [0, 2^12)), COUNT(*) GROUP BY A: multiway vs cascade."""
+    import numpy as np
+    import torch
+    from paper_1905_13376_gb300 import binding, datagen
+    R, S, T = datagen.linear_uniform()
+    adom = 1 << 20
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = lambda rel: tuple(torch.from_numpy(c).to(dev) for c in rel)
+    dR, dS, dT = d(R), d(S), d(T)
+    r = ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom)
+    ms = timed_ms(lambda: ctx.join3_linear(dR, dS, dT, "group_by_a", a_domain=adom, sync=False, out=r),
+                  stream, max(args.steps, 50))
+    rc = ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom)
+    cexact = torch.equal(rc["counts"], r["counts"])
+    cms = timed_ms(lambda: ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom,
+                                            sync=False), stream, max(args.steps, 20))
+    nI = int((np.bincount(R[1], minlength=1 << 12).astype(np.int64) *
+              np.bincount(S[0], minlength=1 << 12).astype(np.int64)).sum())
+    exact = None
+    if not args.no_cpu_baseline:
+        want = cpu_baseline_linear(R, S, T, adom)
+        exact = int(r["total"].item()) == want["total"] and np.array_equal(r["counts"].cpu().numpy(),
+                                                                           want["counts"])
+    n = 3 * len(R[0])
+    return {"workload": "linear R|x|S|x|T, 2^16 tuples per relation, A,D uniform in [0,2^20), "
+                        "B,C uniform in [0,2^12), COUNT(*) GROUP BY A",
+            "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "result_total": int(r["total"].item()),
+            "cascade": {"ms_per_step": cms, "value": n / (cms * 1e-3), "intermediate_rows": nI,
+                        "exact_match_multiway": bool(cexact)},
+            "multiway_speedup": cms / ms, "exact_vs_oracle": exact}
+
+
+def run_triangles(ctx, stream, args, pk):
+    """Cyclic join R(A,B) S(B,C) T(C,A) on the 2^22-vertex power-law graph
+    (edges oriented a < b, T the reversed edges): total, GROUP BY A, the
+    materialised triangle list (capacity from the count) and the cascade of
+    binary joins, run in chunks of its intermediate."""
+    import numpy as np
+    import torch
+    from paper_1905_13376_gb300 import binding, datagen
+    a, b = datagen.chung_lu_undirected()
+    R, S, T = datagen.triangle_relations(a, b)
+    n_v = 1 << 22
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = lambda rel: tuple(torch.from_numpy(np.ascontiguousarray(c)).to(dev) for c in rel)
+    dR, dS, dT = d(R), d(S), d(T)
+    wedges = int((np.bincount(b, minlength=n_v).astype(np.int64) *
+                  np.bincount(a, minlength=n_v).astype(np.int64)).sum())   # |R join S| on B
+    steps = max(3, args.steps // 4)
+    rc = ctx.join3_cyclic(dR, dS, dT, "count")
+    total = int(rc["total"].item())
+    cms = timed_ms(lambda: ctx.join3_cyclic(dR, dS, dT, "count", sync=False, out=rc), stream, steps, warm=2)
+    rg = ctx.join3_cyclic(dR, dS, dT, "group_by_a", a_domain=n_v)
+    gms = timed_ms(lambda: ctx.join3_cyclic(dR, dS, dT, "group_by_a", a_domain=n_v, sync=False, out=rg),
+                   stream, steps, warm=2)
+    counts = rg["counts"].cpu().numpy()
+    ph = profiled(ctx, lambda: ctx.join3_cyclic(dR, dS, dT, "count", sync=False, out=rc), 2)
+    # the materialised list
+    rr = ctx.join3_cyclic(dR, dS, dT, "rows", capacity=total)
+    n_rows = int(rr["n_rows"].item())
+    g = np.random.default_rng(1)
+    hubs = np.argsort(-np.bincount(a))[:5].astype(np.int32)
+    sample = np.unique(np.concatenate([g.choice(a, 300), hubs]))
+    rows = rr["rows"]
+    mine = rows[torch.isin(rows[:, 0], torch.from_numpy(sample).to(dev))].cpu().numpy()
+    del rr, rows
+    torch.cuda.synchronize()
+    rms = timed_ms(lambda: ctx.join3_cyclic(dR, dS, dT, "rows", capacity=total, sync=False), stream, 3, warm=1)
+    torch.cuda.empty_cache()
+    # the cascade: I = R |x| S on B, chunked through a 32 GB workspace
+    casc = None
+    if not args.no_cascade:
+        wsb = 32 << 30
+        t0 = time.time()
+        rcas = ctx.cascade_join(binding.MWJ_CYCLIC, dR, dS, dT, "count", workspace_bytes=wsb)
+        torch.cuda.synchronize()
+        c_ms = timed_ms(lambda: ctx.cascade_join(binding.MWJ_CYCLIC, dR, dS, dT, "count", sync=False,
+                                                 workspace_bytes=wsb), stream, 1, warm=0)
+        casc = {"ms_per_step": c_ms, "intermediate_rows": wedges, "intermediate_bytes": 12 * wedges,
+                "workspace_bytes": wsb, "exact_match_multiway": int(rcas["total"].item()) == total,
+                "first_call_s": round(time.time() - t0, 2), "multiway_speedup": c_ms / cms}
+        del rcas
+        ctx._ws = None
+        torch.cuda.empty_cache()
+    # the probe kernel's rate: one wedge check (a (c, a) membership probe in
+    # T_ki's shared-memory set) per R tuple of a bucket per S tuple whose b
+    # it shares; counted once per wedge of R |x| S (tiles split into several
+    # items re-probe, so this is a lower bound of the work).  Peak: every
+    # SM's 32 shared-memory banks serve 128 B per clock, 8 B per probe.
+    pms = ph.get("cyc_probe", (float("nan"), 0))[0]
+    import json as _json
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    fmax = _json.load(open(peaks_file)).get("sm_max_mhz", 2070.0) if os.path.exists(peaks_file) else 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_probes = n_sm * fmax * 1e6 * 128 / 8
+    rate = wedges / (pms * 1e-3)
+    exact = None
+    if not args.no_cpu_baseline:
+        want_counts, want_rows = cpu_baseline_cyclic_sampled(R, S, T, sample, n_v)
+        exact = bool(np.array_equal(counts[sample], want_counts) and
+                     np.array_equal(_sorted_rows(mine), want_rows))
+    nin = len(R[0]) + len(S[0]) + len(T[0])
+    return {"workload": f"cyclic R|x|S|x|T (triangles) on a power-law graph of {n_v} vertices, "
+                        f"{len(a)} undirected edges oriented a<b; R = S = edges, T = reversed edges",
+            "shares": list(ctx.plan_shares(binding.MWJ_CYCLIC, dR, dS, dT)), "result_total": total,
+            "count": {"ms_per_step": cms, "value": nin / (cms * 1e-3), "unit": UNIT},
+            "group_by_a": {"ms_per_step": gms, "value": nin / (gms * 1e-3), "unit": UNIT,
+                           "sum_equals_total": int(counts.sum()) == total},
+            "rows": {"ms_per_step": rms, "n_rows": n_rows, "rows_equal_total": n_rows == total,
+                     "bytes": 12 * n_rows, "result_tuples_per_s": n_rows / (rms * 1e-3)},
+            "cascade": casc,
+            "probe": {"kernel": "cyc_probe", "bound": "smem", "ms_per_step": round(pms, 4),
+                      "wedge_checks": wedges, "achieved": rate, "peak": peak_probes,
+                      "unit": "wedge checks/s", "frac": round(rate / peak_probes, 4),
+                      "peak_derivation": f"{n_sm} SMs x {fmax:.0f} MHz x 128 B/clock of shared memory / 8 B per probe"},
+            "kernels": {k: round(v[0], 4) for k, v in ph.items()},
+            "exact_vs_oracle": exact,
+            "exact_sample": f"{len(sample)} A values (300 drawn from the edge list and the 5 busiest) "
+                            "against the oracle's groups and rows for R restricted to them"}
+
+
+def _sorted_rows(x):
+    import numpy as np
+    x = np.asarray(x)
+    if x.size == 0:
+        return x.reshape(0, x.shape[1] if x.ndim == 2 else 3)
+    return x[np.lexsort(x.T[::-1])]
+
+
+def run_batch(ctx, stream, args):
+    """4096 independent joins (linear and cyclic alternating, sizes
+    log-uniform in [2^8, 2^18], domains in [2^6, 2^20], uniform or Zipf(1.0)
+    keys) in one persistent launch, captured into a CUDA graph and replayed;
+    COUNT(*) per query."""
+    import numpy as np
+    import torch
+    from paper_1905_13376_gb300 import binding, datagen
+    t0 = time.time()
+    qs = datagen.batched_queries(4096)
+    gen_s = time.time() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = lambda rel: tuple(torch.from_numpy(np.ascontiguousarray(c)).to(dev) for c in rel)
+    dq = [(binding.MWJ_LINEAR if q.kind == "linear" else binding.MWJ_CYCLIC, d(q.R), d(q.S), d(q.T))
+          for q in qs]
+    tuples = int(sum(len(q.R[0]) + len(q.S[0]) + len(q.T[0]) for q in qs))
+    b = binding.Batch(ctx, dq)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        b.launch(stream=s)   # binds the workspace (outside the capture)
+    torch.cuda.synchronize()
+    got = b.counts[: b.n].cpu().numpy().copy()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.launch(stream=s)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    replay_same = bool(np.array_equal(b.counts[: b.n].cpu().numpy(), got))
+    sizes = np.array([len(q.R[0]) + len(q.S[0]) + len(q.T[0]) for q in qs])
+    g = np.random.default_rng(4)
+    pick = np.unique(np.concatenate([np.argsort(-sizes)[:8], g.choice(len(qs), 40, replace=False)]))
+    exact = None
+    if not args.no_cpu_baseline:
+        want = cpu_baseline_batch_sampled(qs, pick)
+        exact = all(int(got[i]) == want[int(i)] for i in pick)
+    lin = [i for i, q in enumerate(qs) if q.kind == "linear"]
+    shares_lin = [b.shares(i) for i in lin[:3]]
+    b.close()
+    return {"workload": "4096 joins (linear and cyclic alternating), |R|,|S|,|T| log-uniform in [2^8,2^18], "
+                        "key domains log-uniform in [2^6,2^20], uniform or Zipf(1.0) keys, COUNT(*) per query",
+            "impl": "one persistent partition launch and one persistent join launch over all queries, "
+                    "replayed from a CUDA graph", "input_tuples": tuples,
+            "value": tuples / (ms * 1e-3), "unit": UNIT, "ms_per_launch": ms, "replays": reps,
+            "replay_counts_equal_first_launch": replay_same, "exact_vs_oracle": exact,
+            "exact_sample": f"{len(pick)} queries (the 8 largest and 40 drawn at random)",
+            "example_shares_linear": [list(x) for x in shares_lin], "generation_s": round(gen_s, 1)}
 
 
 def run_star(ctx, stream, args, pk):
@@ -431,48 +873,29 @@ def run_star(ctx, stream, args, pk):
     dR, dS, dT = d(R), d(S), d(T)
     adom = 1 << 16
     nS, nR, nT = len(S[0]), len(R[0]), len(T[0])
-
-    def timed(fn, steps):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
-
     r = ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom)
     # closed form: every fact tuple joins one tuple of each dimension
     inv = np.empty(nR, dtype=np.int64)
     inv[R[1]] = np.arange(nR)
     want = np.bincount(R[0][inv[S[0]]], minlength=adom)
     exact = int(r["total"].item()) == nS and np.array_equal(r["counts"].cpu().numpy(), want)
-    ms = timed(lambda: ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom, sync=False), args.steps)
-    ctx.set_profiling(True)
-    ctx.reset_phase_times()
-    for _ in range(args.steps):
-        ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom, sync=False)
-    torch.cuda.synchronize()
-    ph = ctx.phase_times()
-    ctx.set_profiling(False)
-    probe_ms = ph.get("star_probe_groupby", (float("nan"), 0))[0] / args.steps
+    step = lambda: ctx.join3_star(dR, dS, dT, "group_by_a", a_domain=adom, sync=False)
+    ms = timed_ms(step, stream, args.steps)
+    ph = profiled(ctx, step, args.steps)
+    probe_ms = ph.get("star_probe_groupby", (float("nan"), 0))[0]
     # the probe reads S once (8 B per tuple) and both degree tables once
     slots = lambda n: 1 << max(4, int(np.ceil(np.log2(4 * n))))
     pbytes = 8 * nS + 8 * (slots(nR) + slots(nT))
     ach = pbytes / (probe_ms * 1e-3) / 1e9
     rc = ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom)
     exact = exact and torch.equal(rc["counts"], r["counts"])
-    cms = timed(lambda: ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom,
-                                         sync=False), max(3, args.steps // 4))
+    cms = timed_ms(lambda: ctx.cascade_join(binding.MWJ_LINEAR, dR, dS, dT, "group_by_a", a_domain=adom,
+                                            sync=False), stream, max(3, args.steps // 4))
     return {"workload": f"star join: fact S(B,C) {nS} tuples (foreign keys, sorted by B), "
                         f"dimensions R(A,B), T(C,D) {nR} tuples each (unique keys), "
                         f"COUNT(*) GROUP BY A over 2^16 groups",
             "value": (nS + nR + nT) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "exact_match": bool(exact),
+            "exact_vs_closed_form": bool(exact),
             "probe": {"kernel": "star_probe_groupby", "ms_per_step": round(probe_ms, 4),
                       "algorithmic_bytes": pbytes, "achieved": round(ach, 1), "peak": pk[0],
                       "unit": "GB/s", "frac": round(ach / pk[0], 4), "peak_kind": pk[1]},
@@ -486,8 +909,8 @@ def run_skew(ctx, stream, args):
     factorised sum cnt(a) = sum over (a,b) in R of sum over (b,c) in S of
     deg_T(c)."""
     import numpy as np
-    import torch
     from paper_1905_13376_gb300 import binding, datagen
+    import torch
 
     R, S, T = datagen.skewed_linear()
     n = len(R[0])
@@ -521,8 +944,8 @@ def run_skew(ctx, stream, args):
     return {"workload": f"linear R|x|S|x|T GROUP BY A, {n} tuples per relation, B Zipf(1.5) in R and S "
                         f"(one key map; top key {top:.1%} of S), A, C, D uniform",
             "impl": "one bucket per side; heavy keys summed per CTA in shared memory",
-            "value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "exact_match": bool(exact),
-            "result_total": int(want.sum()),
+            "value": 3 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "exact_vs_factorised_sum": bool(exact), "result_total": int(want.sum()),
             "partitioned": {"impl": "partitioned by H(B) with the heavy keys in one extra bucket",
                             "shares": list(psh), "ms_per_step": pms, "value": 3 * n / (pms * 1e-3)}}
 
@@ -536,17 +959,8 @@ def run_join4(ctx, stream, args, F):
     adom = args.vertices
     r = ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom)
     exact_sum = int(r["counts"].sum().item()) == int(r["total"].item())
-    for _ in range(3):
-        ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom, sync=False)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom, sync=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = timed_ms(lambda: ctx.join4_linear(dF, dF, dF, dF, "group_by_a", a_domain=adom, sync=False),
+                  stream, args.steps)
     n = len(F[0])
     return {"workload": "chain of four relations F|x|F|x|F|x|F, COUNT(*) GROUP BY A, same graph",
             "value": 4 * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
@@ -562,17 +976,7 @@ def run_fm(ctx, stream, args, F):
     dF = tuple(torch.from_numpy(c).to(dev) for c in F)
     adom = args.vertices
     r = ctx.fm_linear(dF, dF, dF, adom)
-    for _ in range(3):
-        ctx.fm_linear(dF, dF, dF, adom, sync=False)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.fm_linear(dF, dF, dF, adom, sync=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = timed_ms(lambda: ctx.fm_linear(dF, dF, dF, adom, sync=False), stream, args.steps)
     n = len(F[0])
     est = r["estimates"]
     return {"workload": "distinct friends of friends of friends per person, PCSA sketches "
@@ -581,16 +985,9 @@ def run_fm(ctx, stream, args, F):
             "median_estimate": float(est.median().item()), "max_estimate": float(est.max().item())}
 
 
-def cpu_baseline(F, a_domain, budget_s=30.0):
-    import oracle
-    t0 = time.perf_counter()
-    oracle.linear(F, F, F, oracle.GROUP_BY_A, a_domain=a_domain)
-    dt = time.perf_counter() - t0
-    n = len(F[0])
-    return {"value": 3 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the full workload once ({3 * n} input tuples, {dt:.2f} s, 1 thread)"}
-
-
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle on the same workload and metric
+# ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -610,7 +1007,9 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded power-law graph)",
-            "config": {"workload": desc, "impl": "CPU oracle, single-threaded C hash join"},
+            "config": {"workload": desc, "tuples_per_step": 3 * n, "l2": L2_NOTE,
+                       "parallelism": f"replicas x{world}"},
+            "plan": {"impl": "CPU oracle, single-threaded C hash join"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"the full workload per step ({3 * n} input tuples)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -626,10 +1025,14 @@ def main():
     ap.add_argument("--vertices", type=int, default=1 << 20)
     ap.add_argument("--shares", type=int, nargs="+", default=None,
                     help="I J [log2 table slots]")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU oracle (timed baseline and exactness flags)")
     ap.add_argument("--no-cascade", action="store_true")
     ap.add_argument("--no-partitioned", action="store_true",
                     help="skip timing the partitioned plan beside the default one")
+    ap.add_argument("--no-shuffled", action="store_true", help="skip the shuffled-rows arm")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the uniform, triangle and batch workloads")
     ap.add_argument("--no-fm", action="store_true",
                     help="skip the Flajolet-Martin sketch arm")
     ap.add_argument("--no-join4", action="store_true",
@@ -660,10 +1063,16 @@ def main():
         __graft_entry__.build()
     if world > 1:
         torch.distributed.barrier()
-    out, F = run_ours(args, rank, world, local_rank)
+    out, F, counts, total = run_ours(args, rank, world, local_rank)
     if rank == 0:
+        out["exact_vs_oracle"] = None
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(F, args.vertices)
+            import numpy as np
+            cb, want = cpu_baseline(F, args.vertices)
+            out["cpu_baseline"] = cb
+            out["exact_vs_oracle"] = bool(want["total"] == total and np.array_equal(want["counts"], counts))
+        if out.get("cascade") and "ms_per_step" in out["cascade"]:
+            out["cascade"]["multiway_speedup"] = out["cascade"]["ms_per_step"] / out["ms_per_step"]
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -245,6 +245,14 @@ mwj_status mwj_join3_linear_noalloc(mwj_rel R, mwj_rel S, mwj_rel T, const mwj_s
  * previous call (MWJ_OK if none) and clear it. */
 mwj_status mwj_stream_status(mwj_ctx *ctx, void *stream);
 
+/* Failure detection check: launch one CTA that waits, with the library's
+ * bounded wait and at most `polls` polls (1 .. 2^24), on a barrier phase
+ * that never completes, then records MWJ_ERR_TIMEOUT in the context's
+ * status word and returns; the next mwj_stream_status reports it and the
+ * context stays usable.  The joins' own waits give up the same way when a
+ * copy does not land within the context's spin_limit.  Stream-ordered. */
+mwj_status mwj_check_bounded_wait(mwj_ctx *ctx, int64_t polls, void *stream);
+
 /* ---- batches of independent joins (COUNT(*) per query) -------------------
  * Thousands of small 3-way joins of uneven sizes, linear and cyclic mixed,
  * run by one persistent join kernel after one persistent partitioning kernel

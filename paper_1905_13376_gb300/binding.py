@@ -97,6 +97,7 @@ _SIGS = {
     "mwj_cascade_join": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
+    "mwj_check_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
     "mwj_join3_linear_noalloc": (ctypes.c_int, [mwj_rel, mwj_rel, mwj_rel,
                                                 ctypes.POINTER(mwj_shares),
                                                 ctypes.POINTER(mwj_out), _P]),
@@ -219,6 +220,13 @@ class Context:
     def set_profiling(self, on: bool = True):
         self._check(self.lib.mwj_set_profiling(self.h, 1 if on else 0))
 
+    def check_bounded_wait(self, polls: int, stream=None):
+        """Run the failure-detection check (a bounded wait on a barrier phase
+        that never completes); returns the status mwj_stream_status reports
+        afterwards (MWJ_ERR_TIMEOUT when the wait gave up)."""
+        self._check(self.lib.mwj_check_bounded_wait(self.h, int(polls), self._stream(stream)))
+        return int(self.lib.mwj_stream_status(self.h, self._stream(stream)))
+
     def launch_count(self) -> int:
         return int(self.lib.mwj_launch_count(self.h))
 
@@ -257,10 +265,23 @@ class Context:
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         return ctypes.c_void_p(s.cuda_stream)
 
-    def _outputs(self, mode, a_domain, capacity, arity):
+    def _outputs(self, mode, a_domain, capacity, arity, reuse=None):
         import torch
         dev = self.device
-        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        if reuse is not None:   # the output tensors of an earlier call with the same mode and sizes
+            o = mwj_out()
+            o.mode = mode
+            o.total = reuse["total"].data_ptr()
+            if mode == MWJ_COUNT_GROUP_BY_A:
+                if reuse["counts"].numel() != int(a_domain):
+                    raise ValueError("out: group_counts of another a_domain")
+                o.group_counts = reuse["counts"].data_ptr()
+                o.a_domain = int(a_domain)
+            if mode == MWJ_MATERIALIZE:
+                raise ValueError("out: reuse is for the aggregate modes")
+            return o, reuse
+        # the library writes the total (and the exact row count) itself
+        total = torch.empty(1, dtype=torch.int64, device=dev)
         o = mwj_out()
         o.mode = mode
         o.total = total.data_ptr()
@@ -281,10 +302,10 @@ class Context:
         return o, res
 
     def _run(self, fn, kind_ws, R, S, T, mode, shares, a_domain, capacity, arity, stream, sync,
-             extra=()):
+             extra=(), out=None):
         if isinstance(mode, str):
             mode = MODES[mode]
-        o, res = self._outputs(mode, a_domain, capacity, arity)
+        o, res = self._outputs(mode, a_domain, capacity, arity, out)
         with_shares = kind_ws in (MWJ_LINEAR, MWJ_CYCLIC, MWJ_STAR)
         nb = self.workspace_size(kind_ws, R, S, T, shares if with_shares else None, mode)
         ws = self.workspace(nb)
@@ -302,13 +323,15 @@ class Context:
         return res
 
     def join3_linear(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
-                     stream=None, sync=True):
+                     stream=None, sync=True, out=None):
         """Linear 3-way join R(A,B) S(B,C) T(C,D).  shares = (H(B) buckets,
         g(C) buckets[, log2 on-chip table slots]); None: one bucket per side
         for "count" and "group_by_a" (T's and S's tables in L2), H(B)
-        buckets from |R| for "rows"."""
+        buckets from |R| for "rows".  out: the result dict of an earlier
+        aggregate call with the same mode and a_domain, whose tensors are
+        written again instead of new ones."""
         return self._run(self.lib.mwj_join3_linear, MWJ_LINEAR, R, S, T, mode, shares, a_domain,
-                         capacity, 4, stream, sync)
+                         capacity, 4, stream, sync, out=out)
 
     def join3_star(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
                    stream=None, sync=True):
@@ -357,9 +380,12 @@ class Context:
         return {"sketches": sk, "estimates": est}
 
     def join3_cyclic(self, R, S, T, mode="count", shares=None, a_domain=None, capacity=0,
-                     stream=None, sync=True):
+                     stream=None, sync=True, out=None):
+        """Cyclic 3-way join R(A,B) S(B,C) T(C,A), T given as (c, a) columns.
+        shares = (H(A), G(B), F(C)) bucket counts; None: the library's cube
+        shares.  out: as for join3_linear."""
         return self._run(self.lib.mwj_join3_cyclic, MWJ_CYCLIC, R, S, T, mode, shares, a_domain,
-                         capacity, 3, stream, sync)
+                         capacity, 3, stream, sync, out=out)
 
     def cascade_join(self, kind, R, S, T, mode="count", a_domain=None, capacity=0, stream=None,
                      sync=True, workspace_bytes=None):

@@ -99,12 +99,12 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
     L = LinLayout{};
     if (p.l2) {   // nothing is partitioned: T's table and S's weight table
         L.img = A.take<uint64_t>(single_table_slots(T.n));
-        L.meta = A.take<uint32_t>(4);
+        L.meta = A.take<uint32_t>(kMetaWords);
         L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
         const size_t ws = w_table_slots(S.n) + 2;
         L.w.W = A.take<unsigned long long>(ws);
         L.w.hi = A.take<uint32_t>(ws);
-        L.w.meta = A.take<uint32_t>(4);
+        L.w.meta = A.take<uint32_t>(kMetaWords);
         L.whll = A.take<unsigned int>(hll_scratch_registers(num_sms));
         L.heavy = A.take<uint32_t>(kHeavyTableWords);
         L.hw = A.take<unsigned long long>(kHeavySlots);
@@ -125,7 +125,7 @@ size_t lin_layout(Arena &A, const LinPlan &p, const mwj_rel &R, const mwj_rel &S
         L.img = A.take<uint64_t>(single_table_slots(T.n));
         L.capT = nullptr;
         L.ekey = L.ecnt = L.ecount = nullptr;
-        L.meta = A.take<uint32_t>(4);
+        L.meta = A.take<uint32_t>(kMetaWords);
         L.hll = A.take<unsigned int>(hll_scratch_registers(num_sms));
     } else {
         if (p.rows) {
@@ -417,21 +417,35 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
     cudaStream_t side2 = ctx->prof.on ? st : ctx->side2;
     if (p.l2) {
         // T's table on the side stream while S's weight table is sized and
-        // cleared here; then the S pass and the R pass
+        // cleared here; then the S pass and the R pass.  T's C values and
+        // S's B values may get the direct-address layout (only these passes
+        // read the two tables).  When T's C column is S's B column (a
+        // self-join such as friends of friends of friends) one pass over it
+        // sizes both tables.
+        L.w.seed = sd.slot;
+        L.w.heavy = L.heavy;
+        const bool same_keys = T.x == S.x && T.n == S.n;
+        if (same_keys) {
+            e = w_table_size(S.x, S.n, L.w, L.whll, w_table_slots(S.n), ctx->dev.num_sms, st, L.meta,
+                             single_table_slots(T.n));
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "table sizes");
+        }
         if ((e = cudaEventRecord(ctx->fork, st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(side, ctx->fork, 0)) != cudaSuccess)
             return cuda_fail(ctx, e, "fork");
-        e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
-                                ctx->status, ctx->dev.num_sms, side);
+        if (same_keys)
+            e = single_table_fill(T.x, T.n, sd.slot2, L.meta, L.img, ctx->status, ctx->dev.num_sms, side);
+        else
+            e = single_table_direct(T.x, T.n, sd.slot2, L.hll, L.meta, L.img, single_table_slots(T.n),
+                                    ctx->status, ctx->dev.num_sms, side, true);
         const cudaError_t ej = cudaEventRecord(ctx->join, side);
         if (ej != cudaSuccess) return cuda_fail(ctx, ej, "join");
         join_guard.armed = true;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "T table");
-        L.w.seed = sd.slot;
-        L.w.heavy = L.heavy;
         if ((e = heavy_detect(R.y, R.n, S.x, S.n, kWHeavyBuckets, L.heavy, L.hw, st)) != cudaSuccess)
             return cuda_fail(ctx, e, "heavy keys");
-        e = w_table_prepare(S.x, S.n, L.w, L.whll, w_table_slots(S.n), ctx->dev.num_sms, st);
+        e = same_keys ? w_table_clear(L.w, ctx->dev.num_sms, st)
+                      : w_table_prepare(S.x, S.n, L.w, L.whll, w_table_slots(S.n), ctx->dev.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "S weight table");
         e = cudaStreamWaitEvent(st, ctx->join, 0);
         join_guard.armed = false;

@@ -22,76 +22,14 @@
 #include "internal.h"
 #include "linear_l2.h"
 #include "skew.h"
+#include "warp_runs.cuh"
 
 namespace mwj {
 namespace {
 
 constexpr int WT = 256;     // threads per CTA
-constexpr int WQ = 4;       // tuples per lane per warp round: one 128-bit load per column
+constexpr int WQ = kRunQ;   // tuples per lane per warp round: one 128-bit load per column
 constexpr uint32_t WCHUNK = 32 * WQ;   // tuples per warp round
-
-// Every run of equal keys in the warp's 128 tuples (lane l holds tuples
-// 4l .. 4l+3, in order), summed exactly (modulo 2^64) and handed to
-// emit(key, sum) once, by one lane; runs with sum 0 are skipped.  Runs that
-// end inside a lane are emitted by it; a run that crosses lanes (through any
-// number of lanes holding nothing else) is summed by a segmented inclusive
-// scan over the lanes and emitted by the lane where it ends.  Only adjacent
-// equal keys merge: sorted inputs get one emission per key and warp, any
-// other order is still exact.  Every lane of the warp calls this.
-template <typename F>
-__device__ __forceinline__ void warp_runs(const int32_t (&k)[WQ], const unsigned long long (&x)[WQ],
-                                          uint32_t m, F &&emit) {
-    const uint32_t lane = threadIdx.x & 31;
-    const bool has = m > 0;
-    // the lane's first run (kf, sf) and last run (kl, run); runs between
-    // them end inside the lane and are emitted here
-    int32_t kf = k[0], kl = k[0];
-    unsigned long long sf = 0, run = 0;
-    uint32_t nruns = 0;
-#pragma unroll
-    for (int q = 0; q < WQ; ++q) {
-        if ((uint32_t)q < m) {
-            if (q > 0 && k[q] != kl) {
-                if (nruns == 0)
-                    sf = run;
-                else if (run)
-                    emit(kl, run);
-                ++nruns;
-                kl = k[q];
-                run = 0;
-            }
-            run += x[q];
-        }
-    }
-    const bool single = (nruns == 0);   // the lane holds one run (or nothing)
-    if (single) sf = run;
-    // the first run continues the previous lane's last run
-    const int32_t pk = __shfl_up_sync(0xffffffffu, kl, 1);
-    const int phas = __shfl_up_sync(0xffffffffu, (int)has, 1);
-    const bool cont = has && lane > 0 && phas && pk == kf;
-    // segmented inclusive scan: a chain starts at a lane that does not
-    // continue its predecessor or holds more than one run (its last run
-    // starts the chain); lanes of one run that continue it add their sum
-    unsigned long long v = has ? run : 0ull;   // single: the lane's only run
-    bool head = !(cont && single);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long pv = __shfl_up_sync(0xffffffffu, v, o);
-        const int ph = __shfl_up_sync(0xffffffffu, (int)head, o);
-        if (lane >= (uint32_t)o && !head) {
-            v += pv;
-            head = ph != 0;
-        }
-    }
-    const unsigned long long prev = __shfl_up_sync(0xffffffffu, v, 1);   // chain through lane - 1
-    const int next_cont = __shfl_down_sync(0xffffffffu, (int)cont, 1);
-    if (!has) return;
-    if (!single) {   // the first run ends inside this lane
-        const unsigned long long s = cont ? prev + sf : sf;
-        if (s) emit(kf, s);
-    }
-    if ((lane == 31 || !next_cont) && v) emit(kl, v);   // the chain ends here
-}
 
 // Tuples [i, i + WQ) of two int32 columns (fewer at the end); returns how
 // many are valid.
@@ -166,19 +104,35 @@ __device__ __forceinline__ void w_add(const WTable &w, uint32_t mask, uint32_t b
     set_status(st, MWJ_ERR_CHECK, 7);   // table full: the sizing step under-estimated
 }
 
+// Direct-address weights (the sizing pass chose that layout for S's B
+// values): w(b) is the plain 64-bit word W[b - min], added to with 64-bit
+// atomics whose results are not needed (exact modulo 2^64, no carry word).
+__device__ __forceinline__ void w_add_direct(unsigned long long *__restrict__ W, uint32_t wmin, uint32_t wspan,
+                                             uint32_t b, unsigned long long x, DevStatus *st) {
+    if (b - wmin < wspan)
+        atomicAdd(W + (b - wmin), x);
+    else
+        set_status(st, MWJ_ERR_CHECK, 9);   // a key outside the range the sizing pass saw
+}
+
 __global__ void k_w_clear(unsigned long long *__restrict__ W, uint32_t *__restrict__ hi,
                           uint32_t *__restrict__ meta) {
-    const uint32_t slots = meta[0] + 1;   // a power of two >= 16
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < slots / 2; s += stride) {
-        ((ulonglong2 *)W)[s] = make_ulonglong2(kEmpty64, kEmpty64);
-        ((uint2 *)hi)[s] = make_uint2(0u, 0u);
+    if (meta[kMetaDense]) {
+        const uint32_t span = meta[kMetaSpan];
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < span; s += stride) W[s] = 0ull;
+    } else {
+        const uint32_t slots = meta[0] + 1;   // a power of two >= 16
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < slots / 2; s += stride) {
+            ((ulonglong2 *)W)[s] = make_ulonglong2(kEmpty64, kEmpty64);
+            ((uint2 *)hi)[s] = make_uint2(0u, 0u);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            W[slots] = 0ull;
+            hi[slots] = 0u;
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        W[slots] = 0ull;
-        hi[slots] = 0u;
-        meta[2] = 0u;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) meta[kMetaWide] = 0u;
 }
 
 // S pass.  Warp-uniform loop: a warp takes 128 consecutive tuples per round,
@@ -186,18 +140,18 @@ __global__ void k_w_clear(unsigned long long *__restrict__ W, uint32_t *__restri
 // Heavy keys (sampled, see heavy_detect) are summed per CTA in shared
 // memory and added to the table once per CTA, so that a key holding a large
 // share of S in no particular order does not funnel every warp's adds into
-// one L2 word.
-__global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, const int32_t *__restrict__ Sc,
-                                                uint32_t n, TImg t, WTable w, DevStatus *st) {
-    __shared__ uint32_t hbuf[kHeavySlots];
-    __shared__ unsigned long long hacc[kHeavySlots];
-    const uint32_t *hs = heavy_to_smem(w.heavy, hbuf);
-    if (hs) {
-        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT) hacc[i] = 0ull;
-        __syncthreads();
-    }
+// one L2 word.  TD / WD: T's table / S's weight table in the direct-address
+// layout (one load per T lookup, one fire-and-forget 64-bit add per run of
+// equal B values) rather than hashed.
+template <bool TD, bool WD>
+__device__ __forceinline__ void w_build_pass(const int32_t *__restrict__ Sb, const int32_t *__restrict__ Sc,
+                                             uint32_t n, const TImg &t, const WTable &w, DevStatus *st,
+                                             const uint32_t *hs, unsigned long long *hacc) {
     const uint32_t tmask = __ldg(t.meta);
     const uint32_t wmask = __ldg(w.meta);
+    const uint32_t tmin = TD ? __ldg(t.meta + kMetaMin) : 0u, tspan = TD ? __ldg(t.meta + kMetaSpan) : 0u;
+    const uint32_t wmin = WD ? __ldg(w.meta + kMetaMin) : 0u, wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
+    const uint32_t *tdeg = (const uint32_t *)t.img;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
     const bool vec = (((uintptr_t)Sb | (uintptr_t)Sc) & 15) == 0;
@@ -212,18 +166,27 @@ __global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, 
         int32_t nb[WQ], nc[WQ];
         uint32_t nm = 0;
         if (nr < rounds) nm = load_pairs(Sb, Sc, n, nr * WCHUNK + lane * WQ, vec, pol, nb, nc);
-        uint32_t ts[WQ];
-        unsigned long long tv[WQ], x[WQ];
+        unsigned long long x[WQ];
+        if constexpr (TD) {
 #pragma unroll
-        for (int q = 0; q < WQ; ++q) {
-            if ((uint32_t)q < m) {
-                ts[q] = slot_of((uint32_t)c[q], t.seed_slot, tmask);
-                tv[q] = __ldg((const unsigned long long *)(t.img + ts[q]));
+            for (int q = 0; q < WQ; ++q) {
+                const uint32_t k = (uint32_t)c[q] - tmin;
+                x[q] = ((uint32_t)q < m && k < tspan) ? (unsigned long long)__ldg(tdeg + k) : 0ull;
             }
-        }
+        } else {
+            uint32_t ts[WQ];
+            unsigned long long tv[WQ];
 #pragma unroll
-        for (int q = 0; q < WQ; ++q)
-            x[q] = ((uint32_t)q < m) ? t_deg(t.img, tmask, (uint32_t)c[q], ts[q], tv[q]) : 0ull;
+            for (int q = 0; q < WQ; ++q) {
+                if ((uint32_t)q < m) {
+                    ts[q] = slot_of((uint32_t)c[q], t.seed_slot, tmask);
+                    tv[q] = __ldg((const unsigned long long *)(t.img + ts[q]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < WQ; ++q)
+                x[q] = ((uint32_t)q < m) ? t_deg(t.img, tmask, (uint32_t)c[q], ts[q], tv[q]) : 0ull;
+        }
         if (hs) {
 #pragma unroll
             for (int q = 0; q < WQ; ++q) {
@@ -235,7 +198,12 @@ __global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, 
                 }
             }
         }
-        warp_runs(b, x, m, [&](int32_t key, unsigned long long s) { w_add(w, wmask, (uint32_t)key, s, st); });
+        warp_runs(b, x, m, [&](int32_t key, unsigned long long sum) {
+            if constexpr (WD)
+                w_add_direct(w.W, wmin, wspan, (uint32_t)key, sum, st);
+            else
+                w_add(w, wmask, (uint32_t)key, sum, st);
+        });
 #pragma unroll
         for (int q = 0; q < WQ; ++q) {
             b[q] = nb[q];
@@ -246,9 +214,50 @@ __global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, 
     }
     if (hs) {
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT)
-            if (hacc[i]) w_add(w, wmask, hbuf[i], hacc[i], st);
+        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT) {
+            if (!hacc[i]) continue;
+            if constexpr (WD)
+                w_add_direct(w.W, wmin, wspan, hs[i], hacc[i], st);
+            else
+                w_add(w, wmask, hs[i], hacc[i], st);
+        }
     }
+}
+
+// Two kernels share the S pass: the direct-address one (both tables in that
+// layout, few registers) and the general one; the call launches both and the
+// one whose layout the sizing passes did not choose returns at once.
+__global__ void __launch_bounds__(WT) k_w_build(const int32_t *__restrict__ Sb, const int32_t *__restrict__ Sc,
+                                                uint32_t n, TImg t, WTable w, DevStatus *st) {
+    const bool td = __ldg(t.meta + kMetaDense) != 0u, wd = __ldg(w.meta + kMetaDense) != 0u;
+    if (td && wd) return;
+    __shared__ uint32_t hbuf[kHeavySlots];
+    __shared__ unsigned long long hacc[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(w.heavy, hbuf);
+    if (hs) {
+        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT) hacc[i] = 0ull;
+        __syncthreads();
+    }
+    if (td)
+        w_build_pass<true, false>(Sb, Sc, n, t, w, st, hs, hacc);
+    else if (wd)
+        w_build_pass<false, true>(Sb, Sc, n, t, w, st, hs, hacc);
+    else
+        w_build_pass<false, false>(Sb, Sc, n, t, w, st, hs, hacc);
+}
+
+__global__ void __launch_bounds__(WT) k_w_build_direct(const int32_t *__restrict__ Sb,
+                                                       const int32_t *__restrict__ Sc, uint32_t n, TImg t,
+                                                       WTable w, DevStatus *st) {
+    if (!__ldg(t.meta + kMetaDense) || !__ldg(w.meta + kMetaDense)) return;
+    __shared__ uint32_t hbuf[kHeavySlots];
+    __shared__ unsigned long long hacc[kHeavySlots];
+    const uint32_t *hs = heavy_to_smem(w.heavy, hbuf);
+    if (hs) {
+        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT) hacc[i] = 0ull;
+        __syncthreads();
+    }
+    w_build_pass<true, true>(Sb, Sc, n, t, w, st, hs, hacc);
 }
 
 // w(b) from the first probe (slot s, value v); 0 when b is not in S.
@@ -266,14 +275,16 @@ __device__ __forceinline__ unsigned long long w_get(const WTable &w, uint32_t ma
 }
 
 // R pass (MODE 0: COUNT, MODE 1: GROUP BY A); same loop as the S pass.
-template <int MODE>
-__global__ void __launch_bounds__(WT) k_w_probe(const int32_t *__restrict__ Ra, const int32_t *__restrict__ Rb,
-                                                uint32_t n, WTable w, int32_t a_domain,
-                                                unsigned long long *__restrict__ cnt,
-                                                unsigned long long *__restrict__ total, DevStatus *st) {
-    __shared__ unsigned long long red[32];
+// WD: the weight table in the direct-address layout.
+template <int MODE, bool WD>
+__device__ __forceinline__ void w_probe_pass(const int32_t *__restrict__ Ra, const int32_t *__restrict__ Rb,
+                                             uint32_t n, const WTable &w, int32_t a_domain,
+                                             unsigned long long *__restrict__ cnt,
+                                             unsigned long long *__restrict__ total, DevStatus *st,
+                                             unsigned long long *red) {
     const uint32_t wmask = __ldg(w.meta);
-    const bool wide = __ldg(w.meta + 2) != 0;
+    const bool wide = !WD && __ldg(w.meta + kMetaWide) != 0;
+    const uint32_t wmin = WD ? __ldg(w.meta + kMetaMin) : 0u, wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
     const bool vec = (((uintptr_t)Ra | (uintptr_t)Rb) & 15) == 0;
@@ -289,28 +300,38 @@ __global__ void __launch_bounds__(WT) k_w_probe(const int32_t *__restrict__ Ra, 
         int32_t na[WQ], nb[WQ];
         uint32_t nm = 0;
         if (nr < rounds) nm = load_pairs(Ra, Rb, n, nr * WCHUNK + lane * WQ, vec, pol, na, nb);
-        uint32_t ws[WQ];
-        unsigned long long wv[WQ], x[WQ];
+        unsigned long long x[WQ];
+        if constexpr (WD) {
 #pragma unroll
-        for (int q = 0; q < WQ; ++q) {
-            if ((uint32_t)q < m) {
-                const uint32_t k = (uint32_t)b[q];
-                ws[q] = (k == kEmptyKey) ? wmask + 1 : slot_of(k, w.seed, wmask);
-                wv[q] = __ldg(w.W + ws[q]);
+            for (int q = 0; q < WQ; ++q) {
+                const uint32_t k = (uint32_t)b[q] - wmin;
+                x[q] = ((uint32_t)q < m && k < wspan) ? __ldg(w.W + k) : 0ull;
+                acc += x[q];
             }
-        }
+        } else {
+            uint32_t ws[WQ];
+            unsigned long long wv[WQ];
 #pragma unroll
-        for (int q = 0; q < WQ; ++q) {
-            x[q] = ((uint32_t)q < m) ? w_get(w, wmask, wide, (uint32_t)b[q], ws[q], wv[q]) : 0ull;
-            acc += x[q];
+            for (int q = 0; q < WQ; ++q) {
+                if ((uint32_t)q < m) {
+                    const uint32_t k = (uint32_t)b[q];
+                    ws[q] = (k == kEmptyKey) ? wmask + 1 : slot_of(k, w.seed, wmask);
+                    wv[q] = __ldg(w.W + ws[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < WQ; ++q) {
+                x[q] = ((uint32_t)q < m) ? w_get(w, wmask, wide, (uint32_t)b[q], ws[q], wv[q]) : 0ull;
+                acc += x[q];
+            }
         }
         if (MODE == 1) {
 #pragma unroll
             for (int q = 0; q < WQ; ++q)
                 if ((uint32_t)q < m && (uint32_t)a[q] >= (uint32_t)a_domain)
                     set_status(st, MWJ_ERR_DOMAIN, a[q]);
-            warp_runs(a, x, m, [&](int32_t key, unsigned long long s) {
-                if ((uint32_t)key < (uint32_t)a_domain) atomicAdd(cnt + key, s);
+            warp_runs(a, x, m, [&](int32_t key, unsigned long long sum) {
+                if ((uint32_t)key < (uint32_t)a_domain) atomicAdd(cnt + key, sum);
             });
         }
 #pragma unroll
@@ -323,6 +344,27 @@ __global__ void __launch_bounds__(WT) k_w_probe(const int32_t *__restrict__ Ra, 
     }
     acc = block_sum_u64(acc, red);
     if (threadIdx.x == 0 && acc) atomicAdd(total, acc);
+}
+
+// The R pass as two kernels in the same way: direct-address weights, hashed.
+template <int MODE>
+__global__ void __launch_bounds__(WT) k_w_probe(const int32_t *__restrict__ Ra, const int32_t *__restrict__ Rb,
+                                                uint32_t n, WTable w, int32_t a_domain,
+                                                unsigned long long *__restrict__ cnt,
+                                                unsigned long long *__restrict__ total, DevStatus *st) {
+    if (__ldg(w.meta + kMetaDense)) return;
+    __shared__ unsigned long long red[32];
+    w_probe_pass<MODE, false>(Ra, Rb, n, w, a_domain, cnt, total, st, red);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(WT) k_w_probe_direct(const int32_t *__restrict__ Ra,
+                                                       const int32_t *__restrict__ Rb, uint32_t n, WTable w,
+                                                       int32_t a_domain, unsigned long long *__restrict__ cnt,
+                                                       unsigned long long *__restrict__ total, DevStatus *st) {
+    if (!__ldg(w.meta + kMetaDense)) return;
+    __shared__ unsigned long long red[32];
+    w_probe_pass<MODE, true>(Ra, Rb, n, w, a_domain, cnt, total, st, red);
 }
 
 // CTAs of a grid-stride pass: every SM filled, no more warps than rounds.
@@ -340,21 +382,35 @@ uint32_t pass_grid(K kernel, uint32_t n, int num_sms) {
 
 size_t w_table_slots(int64_t nS) { return single_table_slots(nS); }
 
-cudaError_t w_table_prepare(const int32_t *Sb, int64_t nS, const WTable &w, unsigned int *hll,
-                            uint64_t reserve_slots, int num_sms, cudaStream_t st) {
-    cudaError_t e = single_table_size(Sb, nS, w.seed, hll, w.meta, reserve_slots, num_sms, st, "w_hll",
-                                      "w_size");
-    if (e != cudaSuccess) return e;
+cudaError_t w_table_size(const int32_t *Sb, int64_t nS, const WTable &w, unsigned int *hll,
+                         uint64_t reserve_slots, int num_sms, cudaStream_t st, uint32_t *tmeta,
+                         uint64_t treserve) {
+    return single_table_size(Sb, nS, w.seed, hll, w.meta, reserve_slots, num_sms, st, "w_hll", "w_size", true,
+                             tmeta, treserve);
+}
+
+cudaError_t w_table_clear(const WTable &w, int num_sms, cudaStream_t st) {
     ProfScope ps_("w_clear", st);
     k_w_clear<<<num_sms * 4, 512, 0, st>>>(w.W, w.hi, w.meta);
     return cudaGetLastError();
 }
 
+cudaError_t w_table_prepare(const int32_t *Sb, int64_t nS, const WTable &w, unsigned int *hll,
+                            uint64_t reserve_slots, int num_sms, cudaStream_t st) {
+    cudaError_t e = w_table_size(Sb, nS, w, hll, reserve_slots, num_sms, st);
+    if (e != cudaSuccess) return e;
+    return w_table_clear(w, num_sms, st);
+}
+
 cudaError_t w_table_build(const int32_t *Sb, const int32_t *Sc, int64_t nS, const TImg &t,
                           const WTable &w, DevStatus *status, int num_sms, cudaStream_t st) {
     if (nS <= 0) return cudaSuccess;
-    ProfScope ps_("w_build", st);
     const uint32_t n = (uint32_t)nS;
+    {
+        ProfScope ps_("w_build", st);
+        k_w_build_direct<<<pass_grid(k_w_build_direct, n, num_sms), WT, 0, st>>>(Sb, Sc, n, t, w, status);
+    }
+    ProfScope ps_("w_build_hashed", st);
     k_w_build<<<pass_grid(k_w_build, n, num_sms), WT, 0, st>>>(Sb, Sc, n, t, w, status);
     return cudaGetLastError();
 }
@@ -365,11 +421,21 @@ cudaError_t w_table_probe(const int32_t *Ra, const int32_t *Rb, int64_t nR, cons
     if (nR <= 0) return cudaSuccess;
     const uint32_t n = (uint32_t)nR;
     if (mode == 1) {
-        ProfScope ps_("w_probe_groupby", st);
+        {
+            ProfScope ps_("w_probe_groupby", st);
+            k_w_probe_direct<1><<<pass_grid(k_w_probe_direct<1>, n, num_sms), WT, 0, st>>>(
+                Ra, Rb, n, w, a_domain, cnt, total, status);
+        }
+        ProfScope ps_("w_probe_groupby_hashed", st);
         k_w_probe<1><<<pass_grid(k_w_probe<1>, n, num_sms), WT, 0, st>>>(Ra, Rb, n, w, a_domain, cnt, total,
                                                                          status);
     } else {
-        ProfScope ps_("w_probe_count", st);
+        {
+            ProfScope ps_("w_probe_count", st);
+            k_w_probe_direct<0><<<pass_grid(k_w_probe_direct<0>, n, num_sms), WT, 0, st>>>(
+                Ra, Rb, n, w, a_domain, cnt, total, status);
+        }
+        ProfScope ps_("w_probe_count_hashed", st);
         k_w_probe<0><<<pass_grid(k_w_probe<0>, n, num_sms), WT, 0, st>>>(Ra, Rb, n, w, a_domain, cnt, total,
                                                                          status);
     }

@@ -13,11 +13,13 @@ namespace mwj {
 //               as a plain 64-bit sum
 //   hi[s]       w(b) >> 32 (touched only when some w(b) reaches 2^32)
 //   meta[0]     mask; meta[1] the distinct-key estimate; meta[2] set to 1
-//               when some hi[] entry is non-zero
+//               when some hi[] entry is non-zero; meta[3..5] the
+//               direct-address layout (tables.h): when the sizing pass chose
+//               it, w(b) is the plain 64-bit word W[b - min] and hi[] is unused
 struct WTable {
     unsigned long long *W;   // w_table_slots(nS) + 2 entries reserved
     uint32_t *hi;            // w_table_slots(nS) + 2 entries reserved
-    uint32_t *meta;          // 4 entries
+    uint32_t *meta;          // kMetaWords entries
     uint32_t seed;
     const uint32_t *heavy;   // heavy B keys of S (heavy_detect's table), or null
 };
@@ -30,9 +32,15 @@ constexpr uint32_t kWHeavyBuckets = 128;
 size_t w_table_slots(int64_t nS);
 
 // Size the table from S's B column (hll: hll_scratch_registers(num_sms) u32)
-// and clear it.
+// and clear it; or the two steps apart.
 cudaError_t w_table_prepare(const int32_t *Sb, int64_t nS, const WTable &w, unsigned int *hll,
                             uint64_t reserve_slots, int num_sms, cudaStream_t st);
+// tmeta (optional): T's single table when its C column is S's B column,
+// sized from the same pass (at most treserve slots).
+cudaError_t w_table_size(const int32_t *Sb, int64_t nS, const WTable &w, unsigned int *hll,
+                         uint64_t reserve_slots, int num_sms, cudaStream_t st, uint32_t *tmeta = nullptr,
+                         uint64_t treserve = 0);
+cudaError_t w_table_clear(const WTable &w, int num_sms, cudaStream_t st);
 
 // S pass: w(b) += deg_T(c) for every (b, c) of S, T's single table t
 // (t.J == 0) already built.

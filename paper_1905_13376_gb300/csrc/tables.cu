@@ -19,8 +19,11 @@
 // A bucket whose distinct keys overflow the shared-memory table is handled
 // in pieces (the table is flushed and restarted), and the global insert adds
 // the partial counts together, so any skew stays exact.
+#include <climits>
+
 #include "internal.h"
 #include "tables.h"
+#include "warp_runs.cuh"
 
 namespace mwj {
 namespace {
@@ -159,14 +162,18 @@ __global__ void k_tsize(const uint32_t *__restrict__ ecount, uint32_t J, uint32_
         while (cap < 2 * s) cap <<= 1;
         meta[0] = (uint32_t)(cap - 1);   // mask
         meta[1] = (uint32_t)s;
+        meta[kMetaDense] = 0u;           // hashed slots
     }
 }
 
+// Empty hashed slots, or zero degrees of the direct-address layout.
 __global__ void k_tclear(unsigned long long *__restrict__ tbl, const uint32_t *__restrict__ meta) {
-    const uint64_t cap = (uint64_t)meta[0] + 1;
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < cap;
+    const bool dense = meta[kMetaDense] != 0u;
+    const uint64_t words = dense ? ((uint64_t)meta[kMetaSpan] + 1) / 2 : (uint64_t)meta[0] + 1;
+    const unsigned long long fill = dense ? 0ull : kEmpty64;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < words;
          s += (uint64_t)gridDim.x * blockDim.x)
-        tbl[s] = kEmpty64;
+        tbl[s] = fill;
 }
 
 __global__ void __launch_bounds__(BT) k_tinsert(const uint32_t *__restrict__ ekey,
@@ -382,31 +389,48 @@ constexpr uint32_t HLL_M = 1u << HLL_BITS;
 // h >> (32 - HLL_BITS) keeps the largest rank (position of the first 1 bit)
 // of the remaining bits.  mix32 is a bijection of 32-bit keys, so distinct
 // keys have distinct hashes.
+// With mm != null the CTA also leaves the smallest and largest key it saw in
+// mm[2 b], mm[2 b + 1] (b = blockIdx.x; INT32_MAX, INT32_MIN when it saw none).
 __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, uint32_t n,
                                             uint32_t seed, unsigned int *__restrict__ regs,
-                                            unsigned int *__restrict__ done) {
+                                            unsigned int *__restrict__ done, int32_t *__restrict__ mm) {
     __shared__ unsigned int r[HLL_M];
+    __shared__ int32_t smin, smax;
     if (done && blockIdx.x == 0 && threadIdx.x == 0) *done = 0;   // for k_hll_merge_size
     for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) r[j] = 0;
+    if (threadIdx.x == 0) {
+        smin = INT32_MAX;
+        smax = INT32_MIN;
+    }
+    int32_t kmin = INT32_MAX, kmax = INT32_MIN;
     __syncthreads();
     const bool vec = ((uintptr_t)keys & 15) == 0;
     const uint64_t pol = l2_evict_first();
-    const uint32_t stride = gridDim.x * BT * 4;
-    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * 4; i < n; i += stride) {
-        int32_t v[4];
-        if (vec && i + 3 < n) {
-            int4 q = ld_stream((const int4 *)(keys + i), pol);
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    // strips of 16 consecutive keys, one per thread and iteration (four
+    // 16-byte loads in flight), so that a run of equal keys (edge lists come
+    // sorted by source) costs one register update per strip: a register only
+    // grows, so a key equal to its predecessor changes nothing
+    const uint32_t nst = (n + 15) / 16;
+    const uint32_t T = gridDim.x * BT;
+    for (uint32_t c = blockIdx.x * BT + threadIdx.x; c < nst; c += T) {
+        const uint32_t i = c * 16;
+        const uint32_t cnt = min(16u, n - i);
+        int32_t v[16];
+        if (cnt == 16 && vec) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int4 q = ld_stream((const int4 *)(keys + i) + g, pol);
+                v[4 * g] = q.x; v[4 * g + 1] = q.y; v[4 * g + 2] = q.z; v[4 * g + 3] = q.w;
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
+            for (int k = 0; k < 16; ++k) v[k] = ((uint32_t)k < cnt) ? __ldg(keys + i + k) : 0;
         }
-        // a register only grows, so a key equal to its predecessor and a rank
-        // the register already holds change nothing (runs of equal keys are
-        // common: edge lists come sorted by source)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i + k >= n) break;
+        for (int k = 0; k < 16; ++k) {
+            if ((uint32_t)k >= cnt) break;
+            kmin = min(kmin, v[k]);
+            kmax = max(kmax, v[k]);
             if (k > 0 && v[k] == v[k - 1]) continue;
             const uint32_t h = mix32((uint32_t)v[k] ^ seed);
             const uint32_t w = h << HLL_BITS;
@@ -415,12 +439,26 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
             if (*(volatile unsigned int *)reg < rank) atomicMax(reg, rank);
         }
     }
+    if (mm) {
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&smin, kmin);
+            atomicMax(&smax, kmax);
+        }
+    }
     __syncthreads();
     // this CTA's registers; the size kernel takes the maximum over CTAs
     for (uint32_t j = threadIdx.x; j < HLL_M; j += BT) regs[(size_t)blockIdx.x * HLL_M + j] = r[j];
+    if (mm && threadIdx.x == 0) {
+        mm[2 * blockIdx.x] = smin;
+        mm[2 * blockIdx.x + 1] = smax;
+    }
 }
 
-constexpr int HLL_CTAS_PER_SM = 4;
+constexpr int HLL_CTAS_PER_SM = 3;
 
 // regs[0..HLL_M) = max over the rows of regs[ctas][HLL_M]
 __global__ void k_hll_merge(unsigned int *__restrict__ regs, uint32_t ctas) {
@@ -442,10 +480,16 @@ constexpr size_t HLL_TAIL = 2 * HLL_MCTAS + HLL_MCTAS + 8;
 // sum(2^-reg) and of the zero count; the last CTA to finish adds the parts
 // in a fixed order (so the estimate does not depend on the finishing order)
 // and writes meta: table of 2^k >= factor x estimate slots (at most
-// `reserve`).
+// `reserve`).  With per-CTA key ranges kr (rows pairs, or null) the keys may
+// instead get the direct-address layout (slot = key - min, no key stored)
+// when their span max - min + 1 is at most the hashed table's slot count:
+// the keys then fill at least 1/(2 factor) of the span, the array is no
+// larger than the hashed table and a lookup is one load with no probing.
 __global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict__ regs, uint32_t rows,
                                                         unsigned int *__restrict__ tail, uint64_t reserve,
-                                                        double factor, uint32_t *__restrict__ meta) {
+                                                        double factor, uint32_t *__restrict__ meta,
+                                                        const int32_t *__restrict__ kr,
+                                                        uint32_t *__restrict__ meta2, uint64_t reserve2) {
     __shared__ unsigned int m[8][HLL_MB];
     __shared__ bool last;
     double *part_s = (double *)tail;
@@ -453,8 +497,17 @@ __global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict
     unsigned int *done = part_z + HLL_MCTAS;
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t j = blockIdx.x * HLL_MB + lane;
+    // eight rows in flight per thread: the rows are independent loads
     unsigned int mx = 0;
-    for (uint32_t r = w; r < rows; r += 8) mx = max(mx, regs[(size_t)r * HLL_M + j]);
+    uint32_t r = w;
+    for (; r + 56 < rows; r += 64) {
+        unsigned int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(regs + (size_t)(r + 8 * u) * HLL_M + j);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = max(mx, v[u]);
+    }
+    for (; r < rows; r += 8) mx = max(mx, __ldcg(regs + (size_t)r * HLL_M + j));
     m[w][lane] = mx;
     __syncthreads();
     if (w == 0) {
@@ -475,61 +528,135 @@ __global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict
         }
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
+    // the last CTA: the parts in a fixed order (lane l adds parts l, l + 32,
+    // ... in turn, then a fixed butterfly), and the key ranges with all threads
+    __shared__ int32_t rlo[8], rhi[8];
     double S = 0.0;
     unsigned int Z = 0;
-    for (uint32_t b = 0; b < gridDim.x; ++b) {
-        S += __ldcg(part_s + b);
-        Z += __ldcg(part_z + b);
+    if (w == 0) {
+        for (uint32_t b = lane; b < gridDim.x; b += 32) {
+            S += __ldcg(part_s + b);
+            Z += __ldcg(part_z + b);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            S += __shfl_xor_sync(0xffffffffu, S, o);
+            Z += __shfl_xor_sync(0xffffffffu, Z, o);
+        }
     }
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    if (kr) {
+        for (uint32_t b = threadIdx.x; b < rows; b += blockDim.x) {
+            lo = min(lo, __ldcg(kr + 2 * b));
+            hi = max(hi, __ldcg(kr + 2 * b + 1));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            rlo[w] = lo;
+            rhi[w] = hi;
+        }
+        __syncthreads();
+        for (uint32_t q = 0; q < blockDim.x / 32; ++q) {
+            lo = min(lo, rlo[q]);
+            hi = max(hi, rhi[q]);
+        }
+    }
+    if (threadIdx.x != 0) return;
     const double mm = (double)HLL_M;
     double E = (0.7213 / (1.0 + 1.079 / mm)) * mm * mm / S;
     if (E <= 2.5 * mm && Z > 0) E = mm * log(mm / (double)Z);   // small-range correction
-    uint64_t cap = 16;
-    while ((double)cap < factor * E && cap < reserve) cap <<= 1;
-    if (cap > reserve) cap = reserve;
-    meta[0] = (uint32_t)(cap - 1);
-    meta[1] = (uint32_t)E;
+    // meta2 (optional): a second table of the same keys, at most reserve2 slots
+    for (int t = 0; t < 2; ++t) {
+        uint32_t *mt = t ? meta2 : meta;
+        const uint64_t res = t ? reserve2 : reserve;
+        if (!mt) continue;
+        uint64_t cap = 16;
+        while ((double)cap < factor * E && cap < res) cap <<= 1;
+        if (cap > res) cap = res;
+        mt[0] = (uint32_t)(cap - 1);
+        mt[1] = (uint32_t)E;
+        uint32_t dense = 0u;
+        if (kr) {
+            const int64_t span = (int64_t)hi - (int64_t)lo + 1;
+            if (lo <= hi && (uint64_t)span <= cap) {
+                dense = 1u;
+                mt[kMetaMin] = (uint32_t)lo;
+                mt[kMetaSpan] = (uint32_t)span;
+            }
+        }
+        mt[kMetaDense] = dense;
+    }
     *done = 0;
 }
 
-// insert T's C column; each thread merges runs of equal keys among 8
-// consecutive tuples before touching the table
+// Insert T's C column.  A warp round is four blocks of 128 consecutive keys
+// (four per lane), all loaded, with the next round's loads issued, before
+// they are used; every run of equal keys in a block is measured once by
+// warp_run_lengths and added to its entry once:
+// hashed slots through single_insert, the direct-address layout as
+// deg[c - min] += run with a 32-bit add whose result is not needed.
 __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict__ keys, uint32_t n,
                                                        uint32_t seed, unsigned long long *__restrict__ tbl,
                                                        const uint32_t *__restrict__ meta, DevStatus *st) {
     const uint32_t mask = meta[0];
+    const bool dense = meta[kMetaDense] != 0u;
+    const uint32_t kmin = dense ? meta[kMetaMin] : 0u, span = dense ? meta[kMetaSpan] : 0u;
+    uint32_t *deg = (uint32_t *)tbl;
     const bool vec = ((uintptr_t)keys & 15) == 0;
     const uint64_t pol = l2_evict_first();
-    constexpr uint32_t K = 8;
-    const uint32_t stride = gridDim.x * BT * K;
-    for (uint32_t i = (blockIdx.x * BT + threadIdx.x) * K; i < n; i += stride) {
-        int32_t v[K];
-        if (vec && i + K - 1 < n) {
-#pragma unroll
-            for (uint32_t q = 0; q < K / 4; ++q) {
-                int4 a = ld_stream((const int4 *)(keys + i) + q, pol);
-                v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
-            }
-        } else {
-#pragma unroll
-            for (uint32_t k = 0; k < K; ++k) v[k] = (i + k < n) ? __ldg(keys + i + k) : 0;
+    constexpr uint32_t CH = 32 * kRunQ;   // keys of one warp_runs block
+    constexpr int G = 4;                  // blocks per warp round, loaded together
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * BT + threadIdx.x) >> 5, warps = (gridDim.x * BT) >> 5;
+    const uint32_t blocks = (n + CH - 1) / CH;
+    const uint32_t rounds = (blocks + G - 1) / G;
+    auto load = [&](uint32_t blk, int32_t (&v)[kRunQ]) -> uint32_t {
+        const uint32_t i = blk * CH + lane * kRunQ;
+        if (blk >= blocks || i >= n) return 0u;
+        if (vec && i + kRunQ <= n) {
+            const int4 a = ld_stream((const int4 *)(keys + i), pol);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            return kRunQ;
         }
-        const uint32_t m = min(K, n - i);
-        uint32_t cur = (uint32_t)v[0], run = 1;
+        const uint32_t m = min((uint32_t)kRunQ, n - i);
 #pragma unroll
-        for (uint32_t k = 1; k < K; ++k) {
-            if (k >= m) break;
-            if ((uint32_t)v[k] == cur) {
-                ++run;
-            } else {
-                single_insert(tbl, mask, cur, seed, run, st);
-                cur = (uint32_t)v[k];
-                run = 1;
-            }
+        for (int q = 0; q < kRunQ; ++q)
+            if ((uint32_t)q < m) v[q] = __ldg(keys + i + q);
+        return m;
+    };
+    auto emit = [&](int32_t key, uint32_t run) {
+        const uint32_t k = (uint32_t)key;
+        if (!dense)
+            single_insert(tbl, mask, k, seed, (uint32_t)run, st);
+        else if (k - kmin < span)
+            atomicAdd(deg + (k - kmin), (uint32_t)run);
+        else
+            set_status(st, MWJ_ERR_CHECK, 8);   // a key outside the range the sizing pass saw
+    };
+    int32_t v[G][kRunQ];
+    uint32_t m[G];
+    uint32_t r = warp;
+#pragma unroll
+    for (int g = 0; g < G; ++g) m[g] = load(r * G + g, v[g]);
+    while (r < rounds) {
+        const uint32_t nr = r + warps;
+        int32_t nv[G][kRunQ];
+        uint32_t nm[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) nm[g] = load(nr * G + g, nv[g]);
+#pragma unroll
+        for (int g = 0; g < G; ++g) warp_run_lengths(v[g], m[g], emit);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            m[g] = nm[g];
+#pragma unroll
+            for (int q = 0; q < kRunQ; ++q) v[g][q] = nv[g][q];
         }
-        single_insert(tbl, mask, cur, seed, run, st);
+        r = nr;
     }
 }
 
@@ -537,40 +664,49 @@ __global__ void __launch_bounds__(BT) k_tinsert_direct(const int32_t *__restrict
 
 cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
                               uint32_t *meta, uint64_t reserve_slots, int num_sms, cudaStream_t st,
-                              const char *hll_name, const char *size_name) {
+                              const char *hll_name, const char *size_name, bool allow_dense,
+                              uint32_t *meta2, uint64_t reserve2) {
     cudaError_t e;
     const uint32_t nn = (uint32_t)n;
     const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
     unsigned int *tail = hll_regs + (size_t)ctas * HLL_M;
     unsigned int *done = tail + 3 * HLL_MCTAS;
+    int32_t *mm = (allow_dense && nn > 0) ? (int32_t *)(tail + HLL_TAIL) : nullptr;
     uint32_t rows = ctas;
     if (nn > 0) {
         ProfScope ps_(hll_name, st);
-        k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs, done);
+        k_hll<<<ctas, BT, 0, st>>>(keys, nn, seed, hll_regs, done, mm);
     } else {
         rows = 1;
         if ((e = cudaMemsetAsync(hll_regs, 0, HLL_M * sizeof(unsigned int), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(done, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     }
     ProfScope ps_(size_name, st);
-    k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor, meta);
+    k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor, meta,
+                                                 mm, meta2, reserve2);
     return cudaGetLastError();
 }
 
 cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,
                                 uint32_t *meta, uint64_t *tbl, uint64_t reserve_slots,
-                                DevStatus *status, int num_sms, cudaStream_t st) {
+                                DevStatus *status, int num_sms, cudaStream_t st, bool allow_dense) {
     cudaError_t e;
-    const uint32_t nn = (uint32_t)n;
-    if ((e = single_table_size(keys, n, seed, hll_regs, meta, reserve_slots, num_sms, st)) != cudaSuccess)
+    if ((e = single_table_size(keys, n, seed, hll_regs, meta, reserve_slots, num_sms, st, "t_hll", "t_size",
+                               allow_dense)) != cudaSuccess)
         return e;
+    return single_table_fill(keys, n, seed, meta, tbl, status, num_sms, st);
+}
+
+cudaError_t single_table_fill(const int32_t *keys, int64_t n, uint32_t seed, const uint32_t *meta,
+                              uint64_t *tbl, DevStatus *status, int num_sms, cudaStream_t st) {
+    const uint32_t nn = (uint32_t)n;
     {
         ProfScope ps_("t_clear", st);
         k_tclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)tbl, meta);
     }
     if (nn > 0) {
         ProfScope ps_("t_insert", st);
-        const uint32_t groups = (nn + 8 * BT - 1) / (8 * BT);
+        const uint32_t groups = (nn + 4 * kRunQ * BT - 1) / (4 * kRunQ * BT);
         const uint32_t grid = groups < (uint32_t)num_sms * 4 ? groups : (uint32_t)num_sms * 4;
         k_tinsert_direct<<<grid, BT, 0, st>>>(keys, nn, seed, (unsigned long long *)tbl, meta, status);
     }
@@ -586,7 +722,7 @@ cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int
         const uint32_t ctas = (uint32_t)num_sms * HLL_CTAS_PER_SM;
         {
             ProfScope ps_("sketch_hll", st);
-            k_hll<<<ctas, BT, 0, st>>>(keys, (uint32_t)n, seed, regs, nullptr);
+            k_hll<<<ctas, BT, 0, st>>>(keys, (uint32_t)n, seed, regs, nullptr, nullptr);
         }
         ProfScope ps_("sketch_hll_merge", st);
         k_hll_merge<<<(HLL_M + 255) / 256, 256, 0, st>>>(regs, ctas);
@@ -596,6 +732,9 @@ cudaError_t hll_regs(const int32_t *keys, int64_t n, uint32_t seed, unsigned int
     return cudaGetLastError();
 }
 
-size_t hll_scratch_registers(int num_sms) { return (size_t)num_sms * HLL_CTAS_PER_SM * HLL_M + HLL_TAIL; }
+size_t hll_scratch_registers(int num_sms) {
+    const size_t ctas = (size_t)num_sms * HLL_CTAS_PER_SM;
+    return ctas * HLL_M + HLL_TAIL + 2 * ctas;   // registers, sizing tail, per-CTA key ranges
+}
 
 }  // namespace mwj

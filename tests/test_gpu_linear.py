@@ -174,6 +174,19 @@ def test_friends_workload_full_size(ctx):
         assert int(got["total"].item()) == want["total"]
 
 
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx):
+    """A wait on a barrier phase that nothing completes gives up after its
+    poll limit: MWJ_ERR_TIMEOUT reaches the host through the status word,
+    which is cleared by reading it, and the next join on the context is exact."""
+    R, S, T = datagen.linear_uniform(n=4000, ad=500, bd=64, cd=64, dd=500, seed=32)
+    want = oracle.linear(R, S, T, oracle.GROUP_BY_A, a_domain=500)
+    for polls in (1, 1000):
+        assert ctx.check_bounded_wait(polls) == binding.MWJ_ERR_TIMEOUT
+        got = ctx.join3_linear(cu(R), cu(S), cu(T), "group_by_a", a_domain=500)
+        assert int(got["total"].item()) == want["total"]
+        assert np.array_equal(got["counts"].cpu().numpy(), want["counts"])
+
+
 def test_bounded_wait_runs_out_then_context_recovers(ctx):
     """A context whose device waits give up after one poll: the partitioned
     plan with R's buckets on chip stages their tiles through bulk copies and

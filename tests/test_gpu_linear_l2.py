@@ -95,6 +95,36 @@ def test_weights_past_2_pow_32(ctx):
     assert int(want["counts"][0]) == 2 * (k * (1 << 16) + 9) > (1 << 33)
 
 
+@pytest.mark.parametrize("t_spread", [False, True])
+@pytest.mark.parametrize("w_spread", [False, True])
+def test_table_layouts(ctx, t_spread, w_spread):
+    """Both layouts of T's table and of S's weight table, in every pairing:
+    the sizing pass gives keys whose range is at most the hashed table's slot
+    count the direct-address layout (entry at key - min), and keys spread
+    wider the hashed one.  One far-away key that joins nothing (a T tuple
+    with C = -2^31, an S tuple with B = 2^30 + 1) spreads a column without
+    changing the result.  Weights reach 2^32 (the hashed layout's carry word
+    and its key -1 slot, the direct layout's plain 64-bit words)."""
+    k = (1 << 16) + 5
+    g = np.random.default_rng(41)
+    Sb = np.concatenate([np.full(k, 7, np.int32), np.full(k, -1, np.int32),
+                         g.integers(-3, 2000, 30000).astype(np.int32)])
+    Sc = np.concatenate([np.full(2 * k, 3, np.int32), g.integers(0, 3000, 30000).astype(np.int32)])
+    Tc = np.concatenate([np.full(1 << 16, 3, np.int32), g.integers(0, 3000, 20000).astype(np.int32)])
+    Td = g.integers(0, 9, len(Tc)).astype(np.int32)
+    if w_spread:
+        Sb = np.append(Sb, np.int32((1 << 30) + 1))
+        Sc = np.append(Sc, np.int32(-5))            # no T tuple has C = -5
+    if t_spread:
+        Tc = np.append(Tc, np.int32(-2 ** 31))      # no S tuple has C = -2^31
+        Td = np.append(Td, np.int32(0))
+    Ra = g.integers(0, 50, 40000).astype(np.int32)
+    Rb = np.concatenate([np.array([7, 7, -1, 5, 7, -1], np.int32),
+                         g.integers(-3, 2100, 40000 - 6).astype(np.int32)])
+    want = check(ctx, (Ra, Rb), (Sb, Sc), (Tc, Td), 50)
+    assert int(want["total"]) > (1 << 33)
+
+
 def test_domain_error(ctx):
     R = (np.array([0, 5, 1], np.int32), np.array([1, 1, 2], np.int32))
     S = (np.array([1, 2], np.int32), np.array([2, 2], np.int32))
