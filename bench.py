@@ -580,10 +580,12 @@ def run_ours(args, rank, world, local_rank):
         "partitioned": part, "cascade": casc, "shuffled": shuf,
     }
     if first and world == 1:
-        out["uniform_2e16"] = None if args.no_configs else guarded("uniform", run_uniform, ctx, stream, args)
-        out["triangles"] = None if args.no_configs else guarded("triangles", run_triangles, ctx, stream, args,
-                                                                (peak, peak_kind))
-        out["batch_4096"] = None if args.no_configs else guarded("batch", run_batch, ctx, stream, args)
+        out["uniform_2e16"] = None if args.no_configs or args.no_uniform else guarded(
+            "uniform", run_uniform, ctx, stream, args)
+        out["triangles"] = None if args.no_configs or args.no_triangles else guarded(
+            "triangles", run_triangles, ctx, stream, args, (peak, peak_kind))
+        out["batch_4096"] = None if args.no_configs or args.no_batch else guarded(
+            "batch", run_batch, ctx, stream, args)
         out["star"] = None if args.no_star else guarded("star", run_star, ctx, stream, args, (peak, peak_kind))
         out["skew"] = None if args.no_skew else guarded("skew", run_skew, ctx, stream, args)
         out["join4"] = None if args.no_join4 else guarded("join4", run_join4, ctx, stream, args, F)
@@ -714,9 +716,9 @@ def run_triangles(ctx, stream, args, pk):
     import numpy as np
     import torch
     from paper_1905_13376_gb300 import binding, datagen
-    a, b = datagen.chung_lu_undirected()
+    n_v = args.triangle_vertices
+    a, b = datagen.chung_lu_undirected(n_vertices=n_v)
     R, S, T = datagen.triangle_relations(a, b)
-    n_v = 1 << 22
     dev = torch.device("cuda", torch.cuda.current_device())
     d = lambda rel: tuple(torch.from_numpy(np.ascontiguousarray(c)).to(dev) for c in rel)
     dR, dS, dT = d(R), d(S), d(T)
@@ -1033,6 +1035,11 @@ def main():
     ap.add_argument("--no-shuffled", action="store_true", help="skip the shuffled-rows arm")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the uniform, triangle and batch workloads")
+    ap.add_argument("--no-uniform", action="store_true", help="skip the 2^16-tuple uniform workload")
+    ap.add_argument("--no-triangles", action="store_true", help="skip the triangle workload")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 4096-query batch")
+    ap.add_argument("--triangle-vertices", type=int, default=1 << 22,
+                    help="vertices of the triangle workload's graph")
     ap.add_argument("--no-fm", action="store_true",
                     help="skip the Flajolet-Martin sketch arm")
     ap.add_argument("--no-join4", action="store_true",

@@ -20,6 +20,47 @@ struct CycArgs {
     DevStatus *st;
 };
 
+// ---- shares (1, 1, z): R whole, grouped by B; S and T split by F(c) ----
+// R grouped by B: b -> [a] lists.  The sizing pass (tables.h) gives B the
+// direct-address layout (entry b - min) or a hashed key table (slot mask + 1
+// holds key -1); deg[e] is entry e's list length and, once built, end[e] the
+// position after its list in alist.
+struct RGroup {
+    const uint32_t *meta;   // kMetaWords
+    uint32_t *keys;         // hashed layout: mask + 2 entries
+    uint32_t *deg;          // entries
+    uint32_t *end;          // entries
+    int32_t *alist;         // |R|
+    uint32_t seed;
+};
+
+struct CycCArgs {
+    RGroup r;
+    const uint2 *Sp;            // S grouped by F(c): (b, c)
+    const uint32_t *offS;       // z + 1
+    const uint2 *Tp;            // T grouped by F(c): (c, a)
+    const uint32_t *offT;       // z + 1
+    uint32_t z;
+    uint32_t seed;              // hash of the on-chip (c, a) sets
+    int32_t a_domain;
+    unsigned long long *cnt;    // GROUP BY A, or null
+    unsigned long long *total;
+    DevStatus *st;
+};
+
+// T tuples a bucket's chunk holds on chip.
+uint32_t cyc_c_tcap();
+// Group R = (a, b) by b (sizing pass over R's B column first).  hll:
+// hll_scratch_registers(num_sms) u32; reserve: the entries the arrays hold;
+// a_domain > 0: every a must lie in [0, a_domain) (MWJ_ERR_DOMAIN).
+cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const RGroup &r, unsigned int *hll,
+                         uint64_t reserve, unsigned int *bump, int32_t a_domain, DevStatus *status, int num_sms,
+                         cudaStream_t st);
+// items: z + 1 u32; bucket_rows: z + 1 u64, bucket_base: z + 2 u64 (row output).
+cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsigned int *counter,
+                      unsigned long long *bucket_rows, unsigned long long *bucket_base, void *scan_tmp64,
+                      int32_t *rows, long long capacity, long long *n_rows, int num_sms, cudaStream_t st);
+
 uint32_t cyc_rcap();
 uint32_t cyc_tcap();
 size_t cyc_probe_smem();

@@ -53,8 +53,10 @@ def test_complete_graph(ctx, n):
 
 
 @pytest.mark.parametrize("shares", [(1, 1, 1), (3, 5, 7), (16, 1, 1), (1, 16, 1), (1, 1, 16),
-                                    (8, 8, 8)])
+                                    (8, 8, 8), (1, 1, 7), (1, 1, 4096)])
 def test_share_invariance(ctx, shares):
+    """Cube tilings (x, y, z) and the C-bucket plan (1, 1, z: R whole, grouped
+    by B; S and T split by F(c)) give the oracle's result."""
     a, b = datagen.chung_lu_undirected(n_vertices=1 << 12, mean_degree=12.0, seed=77)
     R, S, T = datagen.triangle_relations(a, b)
     check_all_modes(ctx, R, S, T, 1 << 12, shares=shares)
@@ -93,6 +95,28 @@ def test_empty(ctx):
     R, S, T = oriented([(0, 1), (1, 2), (0, 2)])
     for args in [(E, S, T), (R, E, T), (R, S, E)]:
         check_all_modes(ctx, *args, a_domain=3)
+
+
+def test_default_plan_is_c_buckets(ctx):
+    a, b = datagen.chung_lu_undirected(n_vertices=1 << 12, mean_degree=12.0, seed=78)
+    R, S, T = datagen.triangle_relations(a, b)
+    sh = ctx.plan_shares(binding.MWJ_CYCLIC, cu(R), cu(S), cu(T))
+    assert sh[0] == 1 and sh[1] == 1 and sh[2] >= 1
+
+
+def test_c_buckets_hashed_b_keys_and_chunks(ctx):
+    """B values spread over int32 (R's grouping takes the hashed layout) and
+    one C value carrying more T tuples than a bucket's on-chip chunk (the
+    bucket is taken in several chunks, S_k streamed past each)."""
+    g = np.random.default_rng(13)
+    n = 30000
+    bvals = g.integers(-2 ** 31, 2 ** 31 - 1, 500).astype(np.int32)
+    R = (g.integers(0, 400, n).astype(np.int32), bvals[g.integers(0, 500, n)])
+    S = (bvals[g.integers(0, 500, n)], np.where(g.random(n) < 0.3, 7, g.integers(0, 100, n)).astype(np.int32))
+    T = (np.concatenate([np.full(20000, 7, np.int32), g.integers(0, 100, 10000).astype(np.int32)]),
+         g.integers(0, 400, 30000).astype(np.int32))
+    for shares in [None, (1, 1, 1), (1, 1, 3)]:
+        check_all_modes(ctx, R, S, T, 400, shares=shares, rows=False)
 
 
 def test_big_tiles_split_into_items(ctx):
