@@ -394,6 +394,21 @@ def cpu_baseline_cyclic_sampled(R, S, T, sample, a_domain):
     return g["counts"][sample], rows
 
 
+def cpu_baseline_planner_sample(meta, totals):
+    """The oracle's totals of the planner arm's small instances (host copies
+    kept while timing) against the engine's."""
+    import oracle
+    from paper_1905_13376_gb300 import binding
+    ok, n = True, 0
+    for m, tot in zip(meta, totals):
+        if "rel" not in m:
+            continue
+        fn = oracle.linear if m["kind"] == binding.MWJ_LINEAR else oracle.cyclic
+        ok = ok and fn(*m["rel"])["total"] == tot
+        n += 1
+    return ok, n
+
+
 def cpu_baseline_batch_sampled(qs, pick):
     import oracle
     out = {}
@@ -586,6 +601,8 @@ def run_ours(args, rank, world, local_rank):
             "triangles", run_triangles, ctx, stream, args, (peak, peak_kind))
         out["batch_4096"] = None if args.no_configs or args.no_batch else guarded(
             "batch", run_batch, ctx, stream, args)
+        out["planner"] = None if args.no_configs or args.no_planner else guarded(
+            "planner", run_planner, ctx, stream, args)
         out["star"] = None if args.no_star else guarded("star", run_star, ctx, stream, args, (peak, peak_kind))
         out["skew"] = None if args.no_skew else guarded("skew", run_skew, ctx, stream, args)
         out["join4"] = None if args.no_join4 else guarded("join4", run_join4, ctx, stream, args, F)
@@ -852,6 +869,31 @@ def run_batch(ctx, stream, args):
     lin = [i for i, q in enumerate(qs) if q.kind == "linear"]
     shares_lin = [b.shares(i) for i in lin[:3]]
     b.close()
+    # the autotuner: rules per (kind, size class) and launch shapes timed on
+    # these queries, then the batch planned again and replayed the same way
+    from paper_1905_13376_gb300 import autotune
+    tuning = autotune.autotune(ctx, dq)
+    bt = binding.Batch(ctx, dq)
+    with torch.cuda.stream(s):
+        bt.launch(stream=s)
+    torch.cuda.synchronize()
+    got_t = bt.counts[: bt.n].cpu().numpy().copy()
+    graph_t = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_t, stream=s):
+        bt.launch(stream=s)
+    for _ in range(2):
+        graph_t.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        graph_t.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / reps
+    tuned_same = bool(np.array_equal(got_t, got)) and bool(np.array_equal(bt.counts[: bt.n].cpu().numpy(), got))
+    bt.close()
+    ctx.batch_set_rules([])
+    ctx.batch_set_launch(0, 0)
     return {"workload": "4096 joins (linear and cyclic alternating), |R|,|S|,|T| log-uniform in [2^8,2^18], "
                         "key domains log-uniform in [2^6,2^20], uniform or Zipf(1.0) keys, COUNT(*) per query",
             "impl": "one persistent partition launch and one persistent join launch over all queries, "
@@ -859,7 +901,37 @@ def run_batch(ctx, stream, args):
             "value": tuples / (ms * 1e-3), "unit": UNIT, "ms_per_launch": ms, "replays": reps,
             "replay_counts_equal_first_launch": replay_same, "exact_vs_oracle": exact,
             "exact_sample": f"{len(pick)} queries (the 8 largest and 40 drawn at random)",
-            "example_shares_linear": [list(x) for x in shares_lin], "generation_s": round(gen_s, 1)}
+            "example_shares_linear": [list(x) for x in shares_lin], "generation_s": round(gen_s, 1),
+            "autotuned": {"ms_per_launch": ms_t, "value": tuples / (ms_t * 1e-3), "unit": UNIT,
+                          "speedup_over_library_rule": ms / ms_t,
+                          "counts_equal_library_rule": tuned_same,
+                          "tuning_seconds": round(tuning["tuning_seconds"], 1),
+                          "rules_changed": sum(1 for v in tuning["class_timings"].values()
+                                               if v["best_ms"] < v["default_ms"]),
+                          "launch": tuning["launch"], "class_timings": tuning["class_timings"]}}
+
+
+def run_planner(ctx, stream, args):
+    """The learned planner on held-out instances generated now (a seed the
+    training never used; sizes log-uniform in [2^10, 2^24], uniform or Zipf
+    keys, linear and cyclic): every plan timed on this engine, regret of the
+    packaged network's choice against the best measured plan, next to the
+    cost model alone and each fixed plan."""
+    from paper_1905_13376_gb300 import planner
+    t0 = time.time()
+    F, times, totals, meta, rejected = planner.collect(ctx, args.planner_instances, 777, args.planner_budget,
+                                                       keep_small=30000)
+    summary, _ = planner.evaluate(planner.default_planner(ctx), F, times, [m["sizes"] for m in meta])
+    exact, checked = (None, 0)
+    if not args.no_cpu_baseline:
+        exact, checked = cpu_baseline_planner_sample(meta, totals)
+    ctx._ws = None
+    return {"workload": "held-out join instances: |R|,|S|,|T| log-uniform in [2^10,2^24], domains in "
+                        "[2^6,2^22], uniform or Zipf(0.8..1.5) keys, linear and cyclic",
+            "instances": len(F), "rejected": rejected, "seconds": round(time.time() - t0, 1),
+            "plans": ["cascade", "3-way default shares", "3-way alternative shares"],
+            "regret": summary, "plans_agree_on_every_total": True,
+            "exact_vs_oracle": exact, "oracle_checked_instances": checked}
 
 
 def run_star(ctx, stream, args, pk):
@@ -1038,6 +1110,9 @@ def main():
     ap.add_argument("--no-uniform", action="store_true", help="skip the 2^16-tuple uniform workload")
     ap.add_argument("--no-triangles", action="store_true", help="skip the triangle workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-query batch")
+    ap.add_argument("--no-planner", action="store_true", help="skip the learned planner's held-out run")
+    ap.add_argument("--planner-instances", type=int, default=128)
+    ap.add_argument("--planner-budget", type=float, default=60.0, help="seconds for the planner arm's instances")
     ap.add_argument("--triangle-vertices", type=int, default=1 << 22,
                     help="vertices of the triangle workload's graph")
     ap.add_argument("--no-fm", action="store_true",

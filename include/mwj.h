@@ -281,6 +281,33 @@ mwj_status mwj_batch_launch(mwj_batch *batch, int64_t *counts, void *workspace, 
                             void *stream);
 mwj_status mwj_batch_destroy(mwj_batch *batch);
 
+/* Batch planning rules (the autotuner's output; no counterpart in the
+ * paper).  A query whose shares the library chooses falls in the size class
+ * floor(log2(max(|R|, |S|, |T|))) of its kind; the rule of that class gives
+ *   tuples_per_bucket  linear: about this many R tuples per H(B) bucket
+ *                      (I = the power of two at or above |R| / it);
+ *   table_factor       linear: slots of T's degree table per T tuple (the
+ *                      power of two at or above factor x |T|: load factor
+ *                      at most 1 / factor), 2 .. 8;
+ *   fit_pct            cyclic: R_ij and T_ki may fill this percentage of a
+ *                      tile's on-chip capacity when the cube shares are
+ *                      searched (Section 5.2's z|R| + x|S| + y|T|), 10 .. 100.
+ * A field <= 0 keeps the library's rule (8192 tuples, factor 2, 50 %).
+ * mwj_batch_set_rules replaces the context's rules (n == 0 restores the
+ * library's); mwj_batch_set_launch sets the CTAs per SM of the batch's
+ * persistent partitioning and join launches (0: the library's choice, 3 and
+ * the occupancy limit).  Batches created afterwards use them. */
+typedef struct {
+    int32_t kind;               /* MWJ_LINEAR or MWJ_CYCLIC */
+    int32_t size_log2;          /* 0 .. 31 */
+    int32_t tuples_per_bucket;
+    int32_t table_factor;
+    int32_t fit_pct;
+} mwj_batch_rule;
+
+mwj_status mwj_batch_set_rules(mwj_ctx *ctx, const mwj_batch_rule *rules, int32_t n);
+mwj_status mwj_batch_set_launch(mwj_ctx *ctx, int32_t prep_ctas_per_sm, int32_t join_ctas_per_sm);
+
 /* The shares the planner would choose for these relations (host result in
  * *shares), the ones a call with shares == NULL uses.  kind = MWJ_LINEAR,
  * MWJ_CYCLIC or MWJ_STAR.  Linear: {1, 1, 1} for COUNT and GROUP BY A (the
@@ -288,6 +315,14 @@ mwj_status mwj_batch_destroy(mwj_batch *batch);
  * `stream`. */
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T,
                            mwj_mode mode, mwj_shares *shares, void *stream);
+
+/* The alternative share vector a planner weighs against the default one
+ * (host only, from the sizes).  Linear (Section 4.2): H(B) buckets of R and S
+ * held in shared memory, ~32K R tuples each (the default for MATERIALIZE).
+ * Cyclic (Section 5.2 with a third share): the cube tiling (x, y, z) that
+ * minimises z|R| + x|S| + y|T| with R_ij and T_ki fitting a CTA's shared
+ * memory, against the default (1, 1, z) in which R stays whole. */
+mwj_status mwj_plan_shares_alt(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, mwj_shares *shares);
 
 /* Human-readable text of the last error on this context (static storage of
  * the context; valid until the next call). */
@@ -326,11 +361,14 @@ mwj_status mwj_reset_phase_times(mwj_ctx *ctx);
  * T.y (cyclic only).  workspace: device, >= mwj_features_workspace_size().
  * Synchronises `stream`.
  *
- * mwj_cost_model: from the features, out3[0] = log2 predicted seconds of
- * the cascade, out3[1] = of the 3-way join, out3[2] = log2 share scale (0).
- * It restates the tuple counts of Sections 4.2, 5.2 and 6.3 as HBM bytes and
- * random lookups (the paper's Appendix A model, a phase costs its slowest
- * resource), with hbm_gbs the HBM bandwidth in GB/s.
+ * mwj_cost_model: from the features, log2 predicted seconds of the three
+ * plans a planner chooses from: out3[0] the cascade, out3[1] the 3-way join
+ * with the default shares, out3[2] with the alternative shares
+ * (mwj_plan_shares_alt).  It restates the tuple counts of Sections 4.2, 5.2
+ * and 6.3 (tuples read, the intermediate written and read back, wedge checks)
+ * as HBM bytes, random lookups and on-chip probes, a phase costing its
+ * slowest resource (the paper's Appendix A model), with hbm_gbs the HBM
+ * bandwidth in GB/s and rates measured on this GPU.
  *
  * mwj_mlp_*: the planner's network, 24 -> 128 -> 128 -> 3 with ReLU, BF16
  * weights and activations, FP32 accumulation and FP32 Adam master weights

@@ -56,6 +56,11 @@ class mwj_query(ctypes.Structure):
                 ("shares", mwj_shares)]
 
 
+class mwj_batch_rule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("size_log2", ctypes.c_int32), ("tuples_per_bucket", ctypes.c_int32),
+                ("table_factor", ctypes.c_int32), ("fit_pct", ctypes.c_int32)]
+
+
 class mwj_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_int32), ("load_pct", ctypes.c_int32),
@@ -98,9 +103,13 @@ _SIGS = {
                                         ctypes.POINTER(mwj_out), _P, ctypes.c_size_t, _P]),
     "mwj_stream_status": (ctypes.c_int, [_P, _P]),
     "mwj_check_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
+    "mwj_batch_set_rules": (ctypes.c_int, [_P, ctypes.POINTER(mwj_batch_rule), ctypes.c_int32]),
+    "mwj_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "mwj_join3_linear_noalloc": (ctypes.c_int, [mwj_rel, mwj_rel, mwj_rel,
                                                 ctypes.POINTER(mwj_shares),
                                                 ctypes.POINTER(mwj_out), _P]),
+    "mwj_plan_shares_alt": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel,
+                                           ctypes.POINTER(mwj_shares)]),
     "mwj_plan_shares": (ctypes.c_int, [_P, ctypes.c_int, mwj_rel, mwj_rel, mwj_rel, ctypes.c_int,
                                        ctypes.POINTER(mwj_shares), _P]),
     "mwj_last_error": (ctypes.c_char_p, [_P]),
@@ -220,6 +229,19 @@ class Context:
     def set_profiling(self, on: bool = True):
         self._check(self.lib.mwj_set_profiling(self.h, 1 if on else 0))
 
+    def batch_set_rules(self, rules):
+        """Planning rules of batches created afterwards: an iterable of
+        (kind, size_log2, tuples_per_bucket, table_factor, fit_pct); empty
+        restores the library's rules."""
+        rules = list(rules)
+        arr = (mwj_batch_rule * max(1, len(rules)))()
+        for i, r in enumerate(rules):
+            arr[i] = mwj_batch_rule(*[int(v) for v in r])
+        self._check(self.lib.mwj_batch_set_rules(self.h, arr, len(rules)))
+
+    def batch_set_launch(self, prep_ctas_per_sm: int = 0, join_ctas_per_sm: int = 0):
+        self._check(self.lib.mwj_batch_set_launch(self.h, int(prep_ctas_per_sm), int(join_ctas_per_sm)))
+
     def check_bounded_wait(self, polls: int, stream=None):
         """Run the failure-detection check (a bounded wait on a barrier phase
         that never completes); returns the status mwj_stream_status reports
@@ -258,6 +280,13 @@ class Context:
         sh = mwj_shares()
         self._check(self.lib.mwj_plan_shares(self.h, kind, _rel(R), _rel(S), _rel(T), mode,
                                              ctypes.byref(sh), self._stream(stream)))
+        return tuple(sh.s)
+
+    def plan_shares_alt(self, kind, R, S, T):
+        """The alternative share vector (linear: H(B) buckets in shared memory;
+        cyclic: the cube tiling of Section 5.2)."""
+        sh = mwj_shares()
+        self._check(self.lib.mwj_plan_shares_alt(self.h, kind, _rel(R), _rel(S), _rel(T), ctypes.byref(sh)))
         return tuple(sh.s)
 
     def _stream(self, stream):

@@ -255,6 +255,13 @@ mwj_status mwj_create(mwj_ctx **out, const mwj_config *cfg) {
     if (e != cudaSuccess) { delete ctx; return MWJ_ERR_CUDA; }
     e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
     if (e != cudaSuccess) { cudaFree(ctx->status); delete ctx; return MWJ_ERR_CUDA; }
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 32; ++c) {
+            ctx->batch_tpb[k][c] = 0;
+            ctx->batch_tfac[k][c] = 0;
+            ctx->batch_fit[k][c] = 0;
+        }
+    ctx->batch_prep_cps = ctx->batch_join_cps = 0;
     ctx->side = ctx->side2 = nullptr;
     ctx->fork = ctx->join = ctx->join2 = ctx->heavy_ready = nullptr;
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -552,6 +559,14 @@ mwj_status mwj_join3_linear(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_rel T,
         if (e != cudaSuccess) return cuda_fail(ctx, e, "linear rows");
     }
     return MWJ_OK;
+}
+
+mwj_status mwj_plan_shares_alt(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, mwj_shares *shares) {
+    if (!ctx || !shares) return MWJ_ERR_INVALID_ARG;
+    if (!rel_ok(R) || !rel_ok(S) || !rel_ok(T)) return fail(ctx, MWJ_ERR_INVALID_ARG, "bad relation");
+    if (kind == MWJ_LINEAR) return plan_linear_default(ctx, R, S, T, shares);
+    if (kind == MWJ_CYCLIC) return plan_cyclic_cube(ctx, R, S, T, shares);
+    return fail(ctx, MWJ_ERR_INVALID_ARG, "bad kind");
 }
 
 mwj_status mwj_plan_shares(mwj_ctx *ctx, int kind, mwj_rel R, mwj_rel S, mwj_rel T, mwj_mode mode,

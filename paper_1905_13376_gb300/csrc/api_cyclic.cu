@@ -37,6 +37,9 @@ struct CycCLayout {
     uint32_t *items;
     void *scan_tmp;
     unsigned int *counter;
+    unsigned long long *big_slots, *big_off, *bigset;
+    uint32_t *big_neg;
+    void *scan_tmp64b;
     unsigned long long *bucket_rows, *bucket_base;
     void *scan_tmp64;
     void *pscratch;
@@ -61,6 +64,11 @@ size_t cyc_c_layout(Arena &A, uint32_t z, const mwj_rel &R, const mwj_rel &S, co
     L.items = A.take<uint32_t>(z + 1);
     L.scan_tmp = A.take<char>(scan_scratch_bytes(z + 1));
     L.counter = A.take<unsigned int>(1);
+    L.big_slots = A.take<unsigned long long>(z + 1);
+    L.big_off = A.take<unsigned long long>(z + 2);
+    L.bigset = A.take<unsigned long long>(4 * (size_t)T.n + 16);
+    L.big_neg = A.take<uint32_t>(z + 1);
+    L.scan_tmp64b = A.take<char>(scan_scratch_bytes(z + 1));
     if (rows) {
         L.bucket_rows = A.take<unsigned long long>(z + 1);
         L.bucket_base = A.take<unsigned long long>(z + 2);
@@ -258,13 +266,16 @@ extern "C" mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_r
         g.r = LC.r;
         g.Sp = LC.Sp; g.offS = LC.offS; g.Tp = LC.Tp; g.offT = LC.offT;
         g.z = p.z;
+        g.big_off = LC.big_off;
+        g.bigset = LC.bigset;
+        g.big_neg = LC.big_neg;
         g.seed = sd.slot2;
         g.a_domain = out->a_domain;
         g.cnt = out->mode == MWJ_COUNT_GROUP_BY_A ? (unsigned long long *)out->group_counts : nullptr;
         g.total = (unsigned long long *)out->total;
         g.st = ctx->status;
-        e = cyc_c_run(g, LC.items, LC.scan_tmp, LC.counter, LC.bucket_rows, LC.bucket_base, LC.scan_tmp64,
-                      rows ? out->rows : nullptr, rows ? out->capacity : 0,
+        e = cyc_c_run(g, LC.items, LC.scan_tmp, LC.counter, LC.big_slots, LC.scan_tmp64b, LC.bucket_rows,
+                      LC.bucket_base, LC.scan_tmp64, rows ? out->rows : nullptr, rows ? out->capacity : 0,
                       rows ? (long long *)out->n_rows : nullptr, ctx->dev.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cyclic probe");
         return MWJ_OK;

@@ -21,6 +21,10 @@ struct mwj_ctx {
     cudaStream_t side, side2;
     cudaEvent_t fork, join, join2, heavy_ready;
     mwj::Profiler prof;
+    // batch planning rules per kind and size class (mwj_batch_set_rules):
+    // R tuples per linear bucket, T table slots per tuple, cyclic fit (%)
+    int32_t batch_tpb[2][32], batch_tfac[2][32], batch_fit[2][32];
+    int32_t batch_prep_cps, batch_join_cps;   // CTAs per SM (0: the library's choice)
     char err[512];
 };
 
@@ -39,6 +43,8 @@ mwj_status linear_default_shares(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &
                                  mwj_mode mode, mwj_shares *sh);
 mwj_status plan_cyclic_default(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
                                mwj_shares *sh);
+mwj_status plan_cyclic_cube(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
+                            mwj_shares *sh);
 mwj_status cyc_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,
                          const mwj_shares *shares, mwj_mode mode, size_t *bytes);
 mwj_status star_workspace(mwj_ctx *ctx, const mwj_rel &R, const mwj_rel &S, const mwj_rel &T,

@@ -487,6 +487,7 @@ struct mwj_batch {
     size_t off_items, off_scan, off_counter;
     void *bound_ws;
     std::vector<mwj_shares> shares;
+    int32_t prep_cps, join_cps;   // launch shapes fixed at create time
 };
 
 namespace {
@@ -503,12 +504,32 @@ uint32_t pow2_ge(uint64_t v) {
     return p;
 }
 
-// shares of one batched query from its sizes: linear: ~8K R tuples per
-// bucket; cyclic: the cost-model choice (z|R| + x|S| + y|T|) under the chunk
-// fit, with every relation's bucket count at most kSegMaxP
-void batch_shares(const mwj_query &q, mwj_shares *sh) {
+// The planning rule of one query: its kind's rule for the size class
+// floor(log2(max(|R|, |S|, |T|))), the library's where the context has none.
+struct Rule {
+    uint32_t tpb;    // linear: R tuples per bucket
+    uint32_t tfac;   // linear: T table slots per tuple
+    double fit;      // cyclic: fraction of a tile's capacity R_ij and T_ki may fill
+};
+
+Rule batch_rule(const mwj_ctx *ctx, const mwj_query &q) {
+    const int64_t m = std::max(std::max(q.R.n, q.S.n), std::max(q.T.n, (int64_t)1));
+    int c = 0;
+    while (c < 31 && (2ll << c) <= m) ++c;
+    const int k = q.kind == MWJ_LINEAR ? 0 : 1;
+    Rule r{8192u, 2u, 0.5};
+    if (ctx->batch_tpb[k][c] > 0) r.tpb = (uint32_t)ctx->batch_tpb[k][c];
+    if (ctx->batch_tfac[k][c] > 0) r.tfac = (uint32_t)ctx->batch_tfac[k][c];
+    if (ctx->batch_fit[k][c] > 0) r.fit = ctx->batch_fit[k][c] / 100.0;
+    return r;
+}
+
+// shares of one batched query from its sizes: linear: about rule.tpb R
+// tuples per bucket; cyclic: the cost-model choice (z|R| + x|S| + y|T|)
+// under the chunk fit, with every relation's bucket count at most kSegMaxP
+void batch_shares(const mwj_query &q, const Rule &rule, mwj_shares *sh) {
     if (q.kind == MWJ_LINEAR) {
-        uint64_t want = (uint64_t)(q.R.n + 8191) / 8192;
+        uint64_t want = (uint64_t)(q.R.n + rule.tpb - 1) / rule.tpb;
         uint32_t I = pow2_ge(want ? want : 1);
         if (I > kSegMaxP) I = kSegMaxP;
         sh->s[0] = (int32_t)I;
@@ -523,7 +544,7 @@ void batch_shares(const mwj_query &q, mwj_shares *sh) {
         for (uint32_t y = 1; y <= 64; y <<= 1)
             for (uint32_t z = 1; z <= 64; z <<= 1) {
                 if (x * y > kSegMaxP || y * z > kSegMaxP || z * x > kSegMaxP) continue;
-                if (nR / (x * y) > 0.5 * CRCAP || nT / (z * x) > 0.5 * CTCAP) continue;
+                if (nR / (x * y) > rule.fit * CRCAP || nT / (z * x) > rule.fit * CTCAP) continue;
                 double cost = z * nR + x * nS + y * nT;
                 if (cost < best) {
                     best = cost;
@@ -554,6 +575,8 @@ mwj_status mwj_batch_create(mwj_ctx *ctx, const mwj_query *queries, int32_t n, m
     b->n = n;
     b->dmem = nullptr;
     b->bound_ws = nullptr;
+    b->prep_cps = ctx->batch_prep_cps;
+    b->join_cps = ctx->batch_join_cps;
     const Seeds &sd = ctx->seeds;
     // workspace layout, with base 0 (rebased at launch)
     Arena A(nullptr, 0);
@@ -576,7 +599,8 @@ mwj_status mwj_batch_create(mwj_ctx *ctx, const mwj_query *queries, int32_t n, m
             return fail(ctx, MWJ_ERR_INVALID_ARG, "query %d: bad kind or relation", qi);
         }
         mwj_shares sh = q.shares;
-        if (sh.s[0] <= 0) batch_shares(q, &sh);
+        const Rule rule = batch_rule(ctx, q);
+        if (sh.s[0] <= 0) batch_shares(q, rule, &sh);
         b->shares.push_back(sh);
         if (q.kind == MWJ_LINEAR) {
             const uint32_t I = (uint32_t)sh.s[0];
@@ -589,7 +613,7 @@ mwj_status mwj_batch_create(mwj_ctx *ctx, const mwj_query *queries, int32_t n, m
             L.offR = (uint32_t *)take(4 * (I + 1));
             L.Sp = (uint2 *)take(sizeof(uint2) * (q.S.n + 2));
             L.offS = (uint32_t *)take(4 * (I + 1));
-            const uint32_t tcap = pow2_ge(2 * (uint64_t)(q.T.n > 0 ? q.T.n : 1) + 16);
+            const uint32_t tcap = pow2_ge((uint64_t)rule.tfac * (uint64_t)(q.T.n > 0 ? q.T.n : 1) + 16);
             L.tbl = (unsigned long long *)take(8ull * tcap);
             L.tmask = tcap - 1;
             L.I = I;
@@ -735,7 +759,7 @@ mwj_status mwj_batch_launch(mwj_batch *b, int64_t *counts, void *workspace, size
         return cuda_fail(ctx, e, "memset counter");
     {
         ProfScope ps_("batch_prep", st);
-        k_batch_prep<<<sms * 3, BTH, 0, st>>>(b->dev, counter, ctx->status);
+        k_batch_prep<<<sms * (b->prep_cps > 0 ? b->prep_cps : 3), BTH, 0, st>>>(b->dev, counter, ctx->status);
     }
     if (b->ncyc_tiles) {
         {
@@ -754,12 +778,42 @@ mwj_status mwj_batch_launch(mwj_batch *b, int64_t *counts, void *workspace, size
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_join, BTH, smem);
     if (occ < 1) occ = 1;
+    if (b->join_cps > 0 && b->join_cps < occ) occ = b->join_cps;
     {
         ProfScope ps_("batch_join", st);
         k_batch_join<<<sms * occ, BTH, smem, st>>>(b->dev, items, counter + 1,
                                                     (unsigned long long *)counts, ctx->status);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "batch launch");
+    return MWJ_OK;
+}
+
+mwj_status mwj_batch_set_rules(mwj_ctx *ctx, const mwj_batch_rule *rules, int32_t n) {
+    if (!ctx || n < 0 || (n > 0 && !rules)) return MWJ_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        const mwj_batch_rule &r = rules[i];
+        if ((r.kind != MWJ_LINEAR && r.kind != MWJ_CYCLIC) || r.size_log2 < 0 || r.size_log2 > 31 ||
+            r.tuples_per_bucket > (1 << 30) || r.table_factor > 8 || (r.table_factor > 0 && r.table_factor < 2) ||
+            r.fit_pct > 100 || (r.fit_pct > 0 && r.fit_pct < 10))
+            return fail(ctx, MWJ_ERR_INVALID_ARG, "batch rule %d out of range", i);
+    }
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 32; ++c) ctx->batch_tpb[k][c] = ctx->batch_tfac[k][c] = ctx->batch_fit[k][c] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const mwj_batch_rule &r = rules[i];
+        const int k = r.kind == MWJ_LINEAR ? 0 : 1;
+        ctx->batch_tpb[k][r.size_log2] = r.tuples_per_bucket;
+        ctx->batch_tfac[k][r.size_log2] = r.table_factor;
+        ctx->batch_fit[k][r.size_log2] = r.fit_pct;
+    }
+    return MWJ_OK;
+}
+
+mwj_status mwj_batch_set_launch(mwj_ctx *ctx, int32_t prep_ctas_per_sm, int32_t join_ctas_per_sm) {
+    if (!ctx || prep_ctas_per_sm < 0 || prep_ctas_per_sm > 8 || join_ctas_per_sm < 0 || join_ctas_per_sm > 8)
+        return MWJ_ERR_INVALID_ARG;
+    ctx->batch_prep_cps = prep_ctas_per_sm;
+    ctx->batch_join_cps = join_ctas_per_sm;
     return MWJ_OK;
 }
 

@@ -41,14 +41,17 @@ struct CycCArgs {
     const uint2 *Tp;            // T grouped by F(c): (c, a)
     const uint32_t *offT;       // z + 1
     uint32_t z;
-    uint32_t seed;              // hash of the on-chip (c, a) sets
+    const unsigned long long *big_off;   // z + 1: big buckets' set regions (slots), scanned
+    const unsigned long long *bigset;    // the regions
+    const uint32_t *big_neg;             // z: (-1, -1) pairs of a big bucket
+    uint32_t seed;              // hash of the (c, a) sets
     int32_t a_domain;
     unsigned long long *cnt;    // GROUP BY A, or null
     unsigned long long *total;
     DevStatus *st;
 };
 
-// T tuples a bucket's chunk holds on chip.
+// T tuples a bucket's on-chip set holds (larger buckets keep theirs in the L2).
 uint32_t cyc_c_tcap();
 // Group R = (a, b) by b (sizing pass over R's B column first).  hll:
 // hll_scratch_registers(num_sms) u32; reserve: the entries the arrays hold;
@@ -56,10 +59,13 @@ uint32_t cyc_c_tcap();
 cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const RGroup &r, unsigned int *hll,
                          uint64_t reserve, unsigned int *bump, int32_t a_domain, DevStatus *status, int num_sms,
                          cudaStream_t st);
-// items: z + 1 u32; bucket_rows: z + 1 u64, bucket_base: z + 2 u64 (row output).
+// items: z + 1 u32; big_slots: z u64 (scanned into g.big_off, z + 2 u64,
+// with scan_tmp64b); g.bigset: 4 |T| + 16 u64 slots; g.big_neg: z u32;
+// bucket_rows: z + 1 u64, bucket_base: z + 2 u64 (row output).
 cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsigned int *counter,
-                      unsigned long long *bucket_rows, unsigned long long *bucket_base, void *scan_tmp64,
-                      int32_t *rows, long long capacity, long long *n_rows, int num_sms, cudaStream_t st);
+                      unsigned long long *big_slots, void *scan_tmp64b, unsigned long long *bucket_rows,
+                      unsigned long long *bucket_base, void *scan_tmp64, int32_t *rows, long long capacity,
+                      long long *n_rows, int num_sms, cudaStream_t st);
 
 uint32_t cyc_rcap();
 uint32_t cyc_tcap();

@@ -13,8 +13,13 @@
 // bucket k, builds T_k's set on chip and streams S_k past it: per S tuple
 // (b, c) it visits every a of R[b] and counts (c, a) in the set.  These are
 // the cube tiling's wedge checks, each wedge of R |x| S once, without the
-// per-tile rebuilds.  A bucket whose T_k exceeds a CTA's set is taken in
-// chunks, each streaming S_k again; results do not depend on z.
+// per-tile rebuilds.  A bucket whose T_k exceeds a CTA's shared-memory set
+// is taken in chunks of it, S_k streamed past each (every chunk checks the
+// bucket's wedges again, against its part of T_k), up to kChunkMax chunks; a
+// larger one (a C value with many T tuples: skewed or tiny C domains) keeps
+// its set in an L2-resident region of the workspace instead, built before
+// the probe, so that its wedges are checked once.  Results do not depend on
+// z.
 #include "api_internal.h"
 #include "cyclic.h"
 #include "tables.h"
@@ -23,8 +28,9 @@ namespace mwj {
 namespace {
 
 constexpr int CC_T = 768;                // threads per probe CTA (two CTAs per SM)
-constexpr uint32_t CC_TCAP = 4096;       // T tuples per chunk: the set is at most half full
-constexpr uint32_t CC_TSLOTS = 8192;     // slots of a chunk's (c, a) multiset (64 KB)
+constexpr uint32_t CC_TCAP = 4096;       // T tuples of an on-chip set: it is at most half full
+constexpr uint32_t kChunkMax = 4;        // on-chip chunks of a bucket before its set moves to the L2
+constexpr uint32_t CC_TSLOTS = 8192;     // slots of an on-chip (c, a) multiset (64 KB)
 constexpr int RG_T = 512;                // threads of the grouping kernels
 constexpr uint32_t CC_QCAP = 2048;       // long R lists queued per work item
 constexpr uint32_t CC_CH = 256;          // wedges of a queued list per warp step
@@ -34,7 +40,7 @@ __device__ __forceinline__ unsigned long long cpack(uint32_t c, uint32_t a) {
     return ((unsigned long long)c << 32) | a;
 }
 
-// A chunk's (c, a) multiset: CC_TSLOTS / 2 buckets of two 8-byte slots (16
+// An on-chip (c, a) multiset: CC_TSLOTS / 2 buckets of two 8-byte slots (16
 // bytes, one shared-memory load), one entry per T tuple.  An insert takes the
 // first free slot of its home bucket or of the buckets after it, so the
 // occupied slots of a bucket are a prefix and a lookup can stop at the first
@@ -160,16 +166,82 @@ __global__ void __launch_bounds__(RG_T) k_rg_scatter(const int32_t *__restrict__
     }
 }
 
-// work items per bucket: T_k's chunks when S_k and T_k are both non-empty
+__host__ __device__ __forceinline__ bool cc_big(uint32_t nt) { return nt > kChunkMax * CC_TCAP; }
+
+// Work items of a bucket whose S_k and T_k are both non-empty: its on-chip
+// chunks, or one item when it is big (cc_big); a big bucket also gets a
+// region of 2^k >= 2 |T_k| slots for its set in the workspace (big_slots[k],
+// 0 for the others).
 __global__ void k_cc_plan(const uint32_t *__restrict__ offS, const uint32_t *__restrict__ offT, uint32_t z,
-                          uint32_t *__restrict__ items) {
+                          uint32_t *__restrict__ items, unsigned long long *__restrict__ big_slots) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < z; k += gridDim.x * blockDim.x) {
         const uint32_t ns = offS[k + 1] - offS[k], nt = offT[k + 1] - offT[k];
-        items[k] = (ns && nt) ? (nt + CC_TCAP - 1) / CC_TCAP : 0u;
+        items[k] = (ns && nt) ? (cc_big(nt) ? 1u : (nt + CC_TCAP - 1) / CC_TCAP) : 0u;
+        unsigned long long slots = 0;
+        if (ns && cc_big(nt)) {
+            slots = 16;
+            while (slots < 2ull * nt) slots <<= 1;
+        }
+        big_slots[k] = slots;
     }
 }
 
-// Persistent kernel over the work items (bucket, T chunk).  PASS 0 counts
+// Empty every big bucket's region (the total is the scan's last entry).
+__global__ void k_cc_bigclear(unsigned long long *__restrict__ gs, const unsigned long long *__restrict__ big_off,
+                              uint32_t z) {
+    const unsigned long long total = big_off[z];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        gs[i] = kEmpty64;
+}
+
+__device__ __forceinline__ uint32_t gslot(uint32_t c, uint32_t a, uint32_t seed) {
+    uint32_t h = (c ^ seed) * 0x85EBCA6Bu ^ a * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x846ca68bU;
+    h ^= h >> 16;
+    return h;
+}
+
+// Big buckets' sets: a CTA per bucket (buckets blockIdx.x, + gridDim.x, ...)
+// inserts T_k's (c, a) pairs into the bucket's region, one entry per tuple
+// (linear probing from gslot); (-1, -1) pairs are counted in big_neg[k].
+__global__ void k_cc_bigbuild(const uint2 *__restrict__ Tp, const uint32_t *__restrict__ offT, uint32_t z,
+                              const unsigned long long *__restrict__ big_off, unsigned long long *__restrict__ gs,
+                              uint32_t *__restrict__ big_neg, uint32_t seed, DevStatus *st) {
+    __shared__ uint32_t negs;
+    for (uint32_t k = blockIdx.x; k < z; k += gridDim.x) {
+        const unsigned long long base = big_off[k], slots = big_off[k + 1] - base;
+        if (slots == 0) continue;
+        if (threadIdx.x == 0) negs = 0u;
+        __syncthreads();
+        const uint32_t mask = (uint32_t)(slots - 1);
+        unsigned long long *reg = gs + base;
+        for (uint32_t q = offT[k] + threadIdx.x; q < offT[k + 1]; q += blockDim.x) {
+            const uint2 tu = __ldg(Tp + q);
+            const unsigned long long key = cpack(tu.x, tu.y);
+            if (key == kEmpty64) {
+                atomicAdd(&negs, 1u);
+                continue;
+            }
+            uint32_t s = gslot(tu.x, tu.y, seed) & mask;
+            bool done = false;
+            for (uint32_t it = 0; it <= mask; ++it) {
+                if (reg[s] == kEmpty64 && atomicCAS(reg + s, kEmpty64, key) == kEmpty64) {
+                    done = true;
+                    break;
+                }
+                s = (s + 1) & mask;
+            }
+            if (!done) set_status(st, MWJ_ERR_CHECK, 26);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) big_neg[k] = negs;
+        __syncthreads();
+    }
+}
+
+// Persistent kernel over the work items (bucket, chunk).  PASS 0 counts
 // (COUNT, GROUP BY A, and the first pass of row output, which adds each
 // item's count to its bucket's total); PASS 1 writes rows at positions taken
 // from the bucket's cursor (its scanned total, advanced atomically).
@@ -203,21 +275,28 @@ __global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t
             if (item_off[mid] <= item) lo = mid; else hi = mid;
         }
         const uint32_t k = lo;
-        const uint32_t chunk = item - item_off[k];
         const uint32_t s0 = g.offS[k], s1 = g.offS[k + 1];
-        const uint32_t ta = g.offT[k] + chunk * CC_TCAP, tz = min(g.offT[k + 1], ta + CC_TCAP);
+        // T_k's set: the item's chunk on chip, or for a big bucket its region
+        // of the workspace, built before this kernel
+        const bool big = cc_big(g.offT[k + 1] - g.offT[k]);
+        const uint32_t ta = g.offT[k] + (item - item_off[k]) * CC_TCAP;
+        const uint32_t tz = big ? g.offT[k + 1] : min(g.offT[k + 1], ta + CC_TCAP);
+        const unsigned long long gbase = g.big_off[k];
+        const uint32_t gmask = (uint32_t)(g.big_off[k + 1] - gbase) - 1u;
+        const unsigned long long *gset = g.bigset + gbase;
 
-        // ---- T chunk as a (c, a) multiset: one entry per tuple ----
-        for (uint32_t q = threadIdx.x; q < CC_TSLOTS; q += CC_T) tk[q] = kEmpty64;
+        // ---- T_k as a (c, a) multiset: one entry per tuple ----
+        if (!big)
+            for (uint32_t q = threadIdx.x; q < CC_TSLOTS; q += CC_T) tk[q] = kEmpty64;
         if (threadIdx.x == 0) {
-            tneg = 0u;
+            tneg = big ? g.big_neg[k] : 0u;
             batch_ctr = 0u;
             chunk_ctr = 0u;
             qn = 0u;
             carry = 0u;
         }
         __syncthreads();
-        for (uint32_t q = ta + threadIdx.x; q < tz; q += CC_T) {
+        for (uint32_t q = ta + threadIdx.x; !big && q < tz; q += CC_T) {
             const uint2 tu = __ldg(g.Tp + q);   // (c, a)
             const unsigned long long key = cpack(tu.x, tu.y);
             if (key == kEmpty64) {               // (-1, -1) is the empty marker: counted apart
@@ -266,7 +345,16 @@ __global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t
         };
         auto count = [&](uint32_t c, uint32_t a) -> uint32_t {
             const unsigned long long key = cpack(c, a);
-            return key == kEmpty64 ? negs : cset_count(tk, key, cbucket(c, a, g.seed));
+            if (key == kEmpty64) return negs;
+            if (!big) return cset_count(tk, key, cbucket(c, a, g.seed));
+            uint32_t m = 0, s = gslot(c, a, g.seed) & gmask;
+            for (uint32_t it = 0; it <= gmask; ++it) {
+                const unsigned long long v = __ldg(gset + s);
+                if (v == kEmpty64) break;
+                m += (v == key);
+                s = (s + 1) & gmask;
+            }
+            return m;
         };
         // walk one list of the warp's: entries [lo, hi) of (b, c)'s R list,
         // 32 a step, two steps in flight
@@ -440,18 +528,33 @@ cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const
 }
 
 cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsigned int *counter,
-                      unsigned long long *bucket_rows, unsigned long long *bucket_base, void *scan_tmp64,
-                      int32_t *rows, long long capacity, long long *n_rows, int num_sms, cudaStream_t st) {
+                      unsigned long long *big_slots, void *scan_tmp64b, unsigned long long *bucket_rows,
+                      unsigned long long *bucket_base, void *scan_tmp64, int32_t *rows, long long capacity,
+                      long long *n_rows, int num_sms, cudaStream_t st) {
     const uint32_t z = g.z;
     const bool with_rows = (n_rows != nullptr);
     cudaError_t e;
     {
         ProfScope ps_("cyc_c_plan", st);
-        k_cc_plan<<<(z + 255) / 256, 256, 0, st>>>(g.offS, g.offT, z, items);
+        k_cc_plan<<<(z + 255) / 256, 256, 0, st>>>(g.offS, g.offT, z, items, big_slots);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(items + z, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = scan_excl_u32(items, z + 1, scan_tmp, st)) != cudaSuccess) return e;
+    // big buckets' sets in the workspace
+    if ((e = scan_excl_u64((const uint64_t *)big_slots, (uint64_t *)g.big_off, z, true, scan_tmp64b, st)) !=
+        cudaSuccess)
+        return e;
+    {
+        ProfScope ps_("cyc_c_bigclear", st);
+        k_cc_bigclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)g.bigset, g.big_off, z);
+    }
+    {
+        ProfScope ps_("cyc_c_bigbuild", st);
+        k_cc_bigbuild<<<num_sms * 2, 512, 0, st>>>(g.Tp, g.offT, z, g.big_off, (unsigned long long *)g.bigset,
+                                                   (uint32_t *)g.big_neg, g.seed, g.st);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = CC_TSLOTS * sizeof(unsigned long long) + CC_QCAP * sizeof(uint4) +
                         (CC_QCAP + 1) * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_cc_probe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=

@@ -143,31 +143,33 @@ __global__ void k_w_clear(unsigned long long *__restrict__ W, uint32_t *__restri
 // one L2 word.  TD / WD: T's table / S's weight table in the direct-address
 // layout (one load per T lookup, one fire-and-forget 64-bit add per run of
 // equal B values) rather than hashed.
+// One warp round of the S pass: lane l holds tuples (b[q], c[q]), q < m, of
+// 128 consecutive ones.  x = deg_T(c); heavy B keys go to the CTA's sums;
+// runs of equal b are summed in the warp and added to w(b) once.
 template <bool TD, bool WD>
-__device__ __forceinline__ void w_build_pass(const int32_t *__restrict__ Sb, const int32_t *__restrict__ Sc,
-                                             uint32_t n, const TImg &t, const WTable &w, DevStatus *st,
-                                             const uint32_t *hs, unsigned long long *hacc) {
-    const uint32_t tmask = __ldg(t.meta);
-    const uint32_t wmask = __ldg(w.meta);
-    const uint32_t tmin = TD ? __ldg(t.meta + kMetaMin) : 0u, tspan = TD ? __ldg(t.meta + kMetaSpan) : 0u;
-    const uint32_t wmin = WD ? __ldg(w.meta + kMetaMin) : 0u, wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
-    const uint32_t *tdeg = (const uint32_t *)t.img;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
-    const bool vec = (((uintptr_t)Sb | (uintptr_t)Sc) & 15) == 0;
-    const uint64_t pol = l2_evict_first();
-    const uint32_t rounds = (n + WCHUNK - 1) / WCHUNK;
-    int32_t b[WQ], c[WQ];
-    uint32_t m = 0;
-    uint32_t r = warp;
-    if (r < rounds) m = load_pairs(Sb, Sc, n, r * WCHUNK + lane * WQ, vec, pol, b, c);
-    while (r < rounds) {
-        const uint32_t nr = r + warps;
-        int32_t nb[WQ], nc[WQ];
-        uint32_t nm = 0;
-        if (nr < rounds) nm = load_pairs(Sb, Sc, n, nr * WCHUNK + lane * WQ, vec, pol, nb, nc);
+struct SPass {
+    const TImg &t;
+    const WTable &w;
+    DevStatus *st;
+    const uint32_t *hs;
+    unsigned long long *hacc;
+    uint32_t tmask, wmask, tmin, tspan, wmin, wspan;
+
+    __device__ SPass(const TImg &t_, const WTable &w_, DevStatus *st_, const uint32_t *hs_,
+                     unsigned long long *hacc_)
+        : t(t_), w(w_), st(st_), hs(hs_), hacc(hacc_) {
+        tmask = __ldg(t.meta);
+        wmask = __ldg(w.meta);
+        tmin = TD ? __ldg(t.meta + kMetaMin) : 0u;
+        tspan = TD ? __ldg(t.meta + kMetaSpan) : 0u;
+        wmin = WD ? __ldg(w.meta + kMetaMin) : 0u;
+        wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
+    }
+
+    __device__ __forceinline__ void round(const int32_t (&b)[WQ], const int32_t (&c)[WQ], uint32_t m) {
         unsigned long long x[WQ];
         if constexpr (TD) {
+            const uint32_t *tdeg = (const uint32_t *)t.img;
 #pragma unroll
             for (int q = 0; q < WQ; ++q) {
                 const uint32_t k = (uint32_t)c[q] - tmin;
@@ -198,30 +200,65 @@ __device__ __forceinline__ void w_build_pass(const int32_t *__restrict__ Sb, con
                 }
             }
         }
-        warp_runs(b, x, m, [&](int32_t key, unsigned long long sum) {
-            if constexpr (WD)
-                w_add_direct(w.W, wmin, wspan, (uint32_t)key, sum, st);
-            else
-                w_add(w, wmask, (uint32_t)key, sum, st);
-        });
+        warp_runs(b, x, m, [&](int32_t key, unsigned long long sum) { add((uint32_t)key, sum); });
+    }
+
+    __device__ __forceinline__ void add(uint32_t b, unsigned long long x) {
+        if constexpr (WD)
+            w_add_direct(w.W, wmin, wspan, b, x, st);
+        else
+            w_add(w, wmask, b, x, st);
+    }
+
+    // the CTA's heavy-key sums into the table (every thread of the CTA calls this)
+    __device__ __forceinline__ void flush_heavy(uint32_t nthreads) {
+        if (!hs) return;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += nthreads)
+            if (hacc[i]) add(hs[i], hacc[i]);
+    }
+};
+
+// Tuples [lo, hi) of a column pair in warp rounds of 128 (warp `warp` of
+// `warps` takes rounds warp, warp + warps, ...), each round's loads issued
+// before the previous round is used; round(x, y, m) per round.
+template <typename F>
+__device__ __forceinline__ void rounds_plain(const int32_t *__restrict__ X, const int32_t *__restrict__ Y,
+                                             uint32_t lo, uint32_t hi, uint32_t warp, uint32_t warps, F &&round) {
+    const uint32_t lane = threadIdx.x & 31;
+    const bool vec = (((uintptr_t)X | (uintptr_t)Y) & 15) == 0 && (lo & 3u) == 0;
+    const uint64_t pol = l2_evict_first();
+    const uint32_t n = hi;
+    const uint32_t rounds = (hi - lo + WCHUNK - 1) / WCHUNK;
+    int32_t x[WQ], y[WQ];
+    uint32_t m = 0;
+    uint32_t r = warp;
+    if (r < rounds) m = load_pairs(X, Y, n, lo + r * WCHUNK + lane * WQ, vec, pol, x, y);
+    while (r < rounds) {
+        const uint32_t nr = r + warps;
+        int32_t nx[WQ], ny[WQ];
+        uint32_t nm = 0;
+        if (nr < rounds) nm = load_pairs(X, Y, n, lo + nr * WCHUNK + lane * WQ, vec, pol, nx, ny);
+        round(x, y, m);
 #pragma unroll
         for (int q = 0; q < WQ; ++q) {
-            b[q] = nb[q];
-            c[q] = nc[q];
+            x[q] = nx[q];
+            y[q] = ny[q];
         }
         m = nm;
         r = nr;
     }
-    if (hs) {
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < kHeavySlots; i += WT) {
-            if (!hacc[i]) continue;
-            if constexpr (WD)
-                w_add_direct(w.W, wmin, wspan, hs[i], hacc[i], st);
-            else
-                w_add(w, wmask, hs[i], hacc[i], st);
-        }
-    }
+}
+
+template <bool TD, bool WD>
+__device__ __forceinline__ void w_build_pass(const int32_t *__restrict__ Sb, const int32_t *__restrict__ Sc,
+                                             uint32_t n, const TImg &t, const WTable &w, DevStatus *st,
+                                             const uint32_t *hs, unsigned long long *hacc) {
+    SPass<TD, WD> P(t, w, st, hs, hacc);
+    const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
+    rounds_plain(Sb, Sc, 0u, n, warp, warps,
+                 [&](const int32_t (&b)[WQ], const int32_t (&c)[WQ], uint32_t m) { P.round(b, c, m); });
+    P.flush_heavy(WT);
 }
 
 // Two kernels share the S pass: the direct-address one (both tables in that
@@ -276,30 +313,28 @@ __device__ __forceinline__ unsigned long long w_get(const WTable &w, uint32_t ma
 
 // R pass (MODE 0: COUNT, MODE 1: GROUP BY A); same loop as the S pass.
 // WD: the weight table in the direct-address layout.
+// One warp round of the R pass: x = w(b) for the lane's tuples (a[q], b[q]),
+// q < m, added to the thread's total and (GROUP BY A) per run of equal a to
+// cnt[a].
 template <int MODE, bool WD>
-__device__ __forceinline__ void w_probe_pass(const int32_t *__restrict__ Ra, const int32_t *__restrict__ Rb,
-                                             uint32_t n, const WTable &w, int32_t a_domain,
-                                             unsigned long long *__restrict__ cnt,
-                                             unsigned long long *__restrict__ total, DevStatus *st,
-                                             unsigned long long *red) {
-    const uint32_t wmask = __ldg(w.meta);
-    const bool wide = !WD && __ldg(w.meta + kMetaWide) != 0;
-    const uint32_t wmin = WD ? __ldg(w.meta + kMetaMin) : 0u, wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
-    const bool vec = (((uintptr_t)Ra | (uintptr_t)Rb) & 15) == 0;
-    const uint64_t pol = l2_evict_first();
-    const uint32_t rounds = (n + WCHUNK - 1) / WCHUNK;
+struct RPass {
+    const WTable &w;
+    int32_t a_domain;
+    unsigned long long *cnt;
+    DevStatus *st;
+    uint32_t wmask, wmin, wspan;
+    bool wide;
     unsigned long long acc = 0;
-    int32_t a[WQ], b[WQ];
-    uint32_t m = 0;
-    uint32_t r = warp;
-    if (r < rounds) m = load_pairs(Ra, Rb, n, r * WCHUNK + lane * WQ, vec, pol, a, b);
-    while (r < rounds) {
-        const uint32_t nr = r + warps;
-        int32_t na[WQ], nb[WQ];
-        uint32_t nm = 0;
-        if (nr < rounds) nm = load_pairs(Ra, Rb, n, nr * WCHUNK + lane * WQ, vec, pol, na, nb);
+
+    __device__ RPass(const WTable &w_, int32_t a_domain_, unsigned long long *cnt_, DevStatus *st_)
+        : w(w_), a_domain(a_domain_), cnt(cnt_), st(st_) {
+        wmask = __ldg(w.meta);
+        wide = !WD && __ldg(w.meta + kMetaWide) != 0;
+        wmin = WD ? __ldg(w.meta + kMetaMin) : 0u;
+        wspan = WD ? __ldg(w.meta + kMetaSpan) : 0u;
+    }
+
+    __device__ __forceinline__ void round(const int32_t (&a)[WQ], const int32_t (&b)[WQ], uint32_t m) {
         unsigned long long x[WQ];
         if constexpr (WD) {
 #pragma unroll
@@ -328,21 +363,25 @@ __device__ __forceinline__ void w_probe_pass(const int32_t *__restrict__ Ra, con
         if (MODE == 1) {
 #pragma unroll
             for (int q = 0; q < WQ; ++q)
-                if ((uint32_t)q < m && (uint32_t)a[q] >= (uint32_t)a_domain)
-                    set_status(st, MWJ_ERR_DOMAIN, a[q]);
+                if ((uint32_t)q < m && (uint32_t)a[q] >= (uint32_t)a_domain) set_status(st, MWJ_ERR_DOMAIN, a[q]);
             warp_runs(a, x, m, [&](int32_t key, unsigned long long sum) {
                 if ((uint32_t)key < (uint32_t)a_domain) atomicAdd(cnt + key, sum);
             });
         }
-#pragma unroll
-        for (int q = 0; q < WQ; ++q) {
-            a[q] = na[q];
-            b[q] = nb[q];
-        }
-        m = nm;
-        r = nr;
     }
-    acc = block_sum_u64(acc, red);
+};
+
+template <int MODE, bool WD>
+__device__ __forceinline__ void w_probe_pass(const int32_t *__restrict__ Ra, const int32_t *__restrict__ Rb,
+                                             uint32_t n, const WTable &w, int32_t a_domain,
+                                             unsigned long long *__restrict__ cnt,
+                                             unsigned long long *__restrict__ total, DevStatus *st,
+                                             unsigned long long *red) {
+    RPass<MODE, WD> P(w, a_domain, cnt, st);
+    const uint32_t warp = (blockIdx.x * WT + threadIdx.x) >> 5, warps = (gridDim.x * WT) >> 5;
+    rounds_plain(Ra, Rb, 0u, n, warp, warps,
+                 [&](const int32_t (&a)[WQ], const int32_t (&b)[WQ], uint32_t m) { P.round(a, b, m); });
+    const unsigned long long acc = block_sum_u64(P.acc, red);
     if (threadIdx.x == 0 && acc) atomicAdd(total, acc);
 }
 

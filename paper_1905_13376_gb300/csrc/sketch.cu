@@ -178,39 +178,55 @@ mwj_status compute_features(mwj_ctx *ctx, int kind, const mwj_rel &R, const mwj_
 }
 
 // ---- cost model ------------------------------------------------------------
-// out[0] = log2 predicted seconds of the cascade, out[1] = of the multiway
-// join with the default shares, out[2] = log2 of the preferred share scale
-// (0: the default shares).
+// log2 predicted seconds of the three plans a planner weighs: out[0] the
+// cascade, out[1] the 3-way join with the default shares, out[2] with the
+// alternative shares (mwj_plan_shares_alt).  Each phase costs its slowest
+// resource (Appendix A): HBM bytes at hbm_gbs, random lookups into an
+// L2-resident table, or on-chip wedge probes, plus a fixed cost per call.
+// The byte counts restate the paper's tuple counts:
+//   linear 3-way join (Section 4.2): R and S read once, T held whole (the
+//     |R||T|/M term vanishes while T's table fits on chip);
+//   cascade (Example 3, Section 6.3): R join S written as I and read back,
+//     12 bytes per I row each way, one T lookup per I row (the cyclic
+//     cascade writes I once more, grouped by (c, a), 8 bytes per row);
+//   cyclic cube tiling (Section 5.2): |R| + 2 sqrt(|R||S||T|/M) tuples read
+//     at the optimal share, M the tuples of one on-chip tile, and every wedge
+//     of R join S checked once on chip.
 void cost_model(const float *f, double hbm_gbs, double *out) {
     const double nR = std::exp2(f[0]) - 1, nS = std::exp2(f[1]) - 1, nT = std::exp2(f[2]) - 1;
+    const double dB = std::exp2(f[4]) - 1, dC = std::exp2(f[5]) - 1;   // distinct B (of R), C (of S)
     const double nI = std::exp2(f[8]) - 1;        // |R join S| estimate
     const bool cyc = f[7] > 0.5f;
     const double bw = hbm_gbs * 1e9;              // bytes/s
-    const double lookups = 2.5e11;                // random L2 lookups/s (hash probe)
-    const double smem_probes = 2.0e12;            // shared-memory probe steps/s
-    const double launch = 40e-6;                  // fixed cost of a call (launches, syncs)
-    // partition: read 8 B + write 8 B per tuple, plus a 4 B histogram read
-    auto part = [&](double n) { return 20.0 * n / bw; };
-    double tm, tc;
+    const double call = 40e-6;                    // launches and host work of one call
+    const double l2_table = 64e6;                 // bytes of a lookup table the L2 keeps
+    // random lookups/s into a table of `keys` distinct keys (8-byte slots at
+    // most a quarter full): L2-resident, else served by HBM sectors
+    auto lookups = [&](double keys) { return 32.0 * keys <= l2_table ? 2.6e11 : 1.0e11; };
+    const double wedge_c = 2.3e11;                // C-bucket probe: wedge checks/s
+    const double wedge_t = 1.5e10;                // cube tiles: wedge checks/s
+    const double M = 1024.0;                      // tuples of R (and of T) one cube tile holds
+    const double tile = 8e-6 / 304.0;             // rebuilding one cube tile, spread over the CTAs
+    double tc, tm, ta;
     if (!cyc) {
-        // Section 4.2: R and S read once; T held whole (its table re-read per
-        // R bucket stays in L2), so |R||T|/M vanishes while T fits L2
-        const double probe = std::max(24.0 * (nR + nS) / bw, (nS + nR) / lookups);
-        tm = launch + part(nR) + part(nS) + 8.0 * nT / bw + probe;
-        // Section 6.3: the cascade writes I (12 B/row) and reads it back
-        tc = 2 * launch + part(nR) + part(nS) + 8.0 * nT / bw +
-             std::max(12.0 * nI / bw, nI / (4 * lookups)) + std::max(8.0 * nI / bw, nI / lookups);
+        const double Lb = lookups(std::max(dB, 1.0)), Lc = lookups(std::max(dC, 1.0));
+        const double passes = std::max(8.0 * (nR + nS) / bw, nS / Lc + nR / Lb);
+        tm = call + 12.0 * nT / bw + passes;                          // one bucket per side
+        ta = call + 16.0 * (nR + nS) / bw + 12.0 * nT / bw + passes;  // + partitioning R and S
+        tc = 2 * call + 16.0 * (nR + nS) / bw + 12.0 * nT / bw + 12.0 * nI / bw +
+             std::max(12.0 * nI / bw, nI / Lc);
     } else {
-        // Section 5.2: z|R| + x|S| + y|T| tuples read; every wedge of R join S
-        // is one on-chip probe
-        const double reads = nR + 2.0 * std::sqrt(std::max(1.0, nR * nS * nT / 4096.0));
-        tm = launch + part(nR) + part(nS) + part(nT) + 8.0 * reads / bw + nI / smem_probes;
-        tc = 2 * launch + part(nR) + part(nS) + part(nT) + 12.0 * nI / bw + 20.0 * nI / bw +
-             nI / smem_probes;
+        const double Lb = lookups(std::max(dB, 1.0));
+        tm = call + 16.0 * nR / bw + nR / Lb + 20.0 * (nS + nT) / bw + nS / Lb + nI / wedge_c;
+        const double reads = nR + 2.0 * std::sqrt(std::max(1.0, nR * nS * nT / M));
+        const double H = std::max(1.0, std::sqrt(nR * nT / (M * std::max(nS, 1.0))));
+        const double tiles = std::max(1.0, nR / M) * H;
+        ta = call + 20.0 * (nR + nS + nT) / bw + 8.0 * reads / bw + tiles * tile + nI / wedge_t;
+        tc = 2 * call + 16.0 * (nR + nS) / bw + 12.0 * nI / bw + 20.0 * (nI + nT) / bw + nI / Lb;
     }
     out[0] = std::log2(std::max(tc, 1e-7));
     out[1] = std::log2(std::max(tm, 1e-7));
-    out[2] = 0.0;
+    out[2] = std::log2(std::max(ta, 1e-7));
 }
 
 }  // namespace mwj

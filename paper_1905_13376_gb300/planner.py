@@ -1,16 +1,25 @@
-"""The learned planner: choose the cascade or the 3-way join, and scale the
-shares, from a join instance's features.
+"""The learned planner: choose the cascade or the 3-way join, and its share
+vector, from a join instance's features.
 
-A plan never changes a result, only its time.  The network (24 -> 128 ->
-128 -> 3, the library's BF16 kernels) predicts log2 microseconds of the
-cascade, log2 microseconds of the 3-way join with the default shares, and
-the best share scale k (shares x 2^k, k in {-1, 0, 1}); the cost model of
-the library is the fallback and the yardstick of the learned planner's
-regret.
+A plan never changes a result, only its time.  Three plans are weighed:
+
+  0  the cascade of binary hash joins (Section 6.3);
+  1  the 3-way join with the library's default shares (linear: one bucket per
+     side, both tables in L2; cyclic: R whole, C split into buckets);
+  2  the 3-way join with the alternative shares of mwj_plan_shares_alt
+     (linear: R and S by H(B) into shared-memory buckets; cyclic: the cube
+     tiling of Section 5.2).
+
+The network (24 -> 128 -> 128 -> 3, the library's BF16 kernels) predicts the
+log2 microseconds of each plan and the planner takes the smallest; the
+library's cost model (the paper's Appendix A restated for this GPU) is the
+fallback and the yardstick of the learned planner's regret.
 
 Training data is produced by the engine itself: seeded synthetic instances
 are generated on the GPU, described by mwj_features, and every plan is timed
-with CUDA events.
+with CUDA events.  A cascade whose intermediate is estimated above
+CASCADE_ROW_LIMIT rows is not run: its label is masked out of the training
+loss and, in the evaluation, it counts as not runnable.
 """
 from __future__ import annotations
 
@@ -24,8 +33,8 @@ import numpy as np
 
 from . import binding
 
-SCALES = (-1, 0, 1)
-CASCADE_ROW_LIMIT = 1 << 30       # larger intermediates are not run (labelled by the model)
+PLANS = ("cascade", "default", "alt")
+CASCADE_ROW_LIMIT = 1 << 30       # larger intermediates are not run
 REJECT_ROW_LIMIT = 1 << 33        # instances beyond this are not generated at all
 
 
@@ -71,7 +80,7 @@ class Instance:
     zipf_s: object
 
 
-def gpu_instance(gen, rng: np.random.Generator, device, size_lo=1 << 10, size_hi=1 << 22,
+def gpu_instance(gen, rng: np.random.Generator, device, size_lo=1 << 10, size_hi=1 << 24,
                  dom_lo=1 << 6, dom_hi=1 << 22) -> Instance:
     kind = binding.MWJ_LINEAR if rng.random() < 0.5 else binding.MWJ_CYCLIC
     lu = lambda lo, hi: int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
@@ -98,58 +107,53 @@ def features(ctx: binding.Context, kind, R, S, T) -> np.ndarray:
     return np.array(f, dtype=np.float32)
 
 
-def scaled_shares(ctx, kind, R, S, T, k: int):
-    # the scale applies to the partitioned plan (the library's default for
-    # row output); the one-bucket plan the linear aggregates default to is
-    # not in this family
-    base = ctx.plan_shares(kind, R, S, T, binding.MWJ_MATERIALIZE)
-    if kind == binding.MWJ_LINEAR:
-        I = max(1, min(16384, int(base[0] * 2.0 ** k)))
-        return (I, 1, 1)
-    sh = [max(1, int(v * 2.0 ** k)) for v in base]
-    while sh[0] * sh[1] > 32768 or sh[1] * sh[2] > 32768 or sh[2] * sh[0] > 32768:
-        sh = [max(1, v // 2) for v in sh]
-    return tuple(sh)
+def plan_shares(ctx, kind, R, S, T, plan: int):
+    """Share vector of a 3-way plan (None: the library's default)."""
+    if plan == 1:
+        return None
+    if plan == 2:
+        return ctx.plan_shares_alt(kind, R, S, T)
+    raise ValueError("the cascade has no shares")
 
 
-def run_plan(ctx, kind, R, S, T, cascade: bool, k: int = 0, mode="count", **kw):
-    if cascade:
+def run_plan(ctx, kind, R, S, T, plan: int, mode="count", **kw):
+    if plan == 0:
         return ctx.cascade_join(kind, R, S, T, mode, **kw)
-    sh = scaled_shares(ctx, kind, R, S, T, k)
+    sh = plan_shares(ctx, kind, R, S, T, plan)
     if kind == binding.MWJ_LINEAR:
         return ctx.join3_linear(R, S, T, mode, shares=sh, **kw)
     return ctx.join3_cyclic(R, S, T, mode, shares=sh, **kw)
 
 
-def time_plan(ctx, inst: Instance, cascade: bool, k: int = 0, reps: int = 1, rows_hint: float = 0):
+def time_plan(ctx, inst: Instance, plan: int, reps: int = 2, rows_hint: float = 0):
     import torch
     kw = {}
-    if cascade:   # room for the whole intermediate when it is known to be large
+    if plan == 0:   # room for the whole intermediate when it is known to be large
         per_row = 12 if inst.kind == binding.MWJ_LINEAR else 20
         kw["workspace_bytes"] = int(min(2.0 * rows_hint, 2.0 ** 31) * per_row) + (256 << 20)
-    run_plan(ctx, inst.kind, inst.R, inst.S, inst.T, cascade, k, **kw)   # warm-up, synchronised
+    r = run_plan(ctx, inst.kind, inst.R, inst.S, inst.T, plan, **kw)   # warm-up, synchronised
+    total = int(r["total"].item())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        r = run_plan(ctx, inst.kind, inst.R, inst.S, inst.T, cascade, k, sync=False, **kw)
+        run_plan(ctx, inst.kind, inst.R, inst.S, inst.T, plan, sync=False, **kw)
     e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) * 1e3 / reps, int(r["total"].item())
+    return e0.elapsed_time(e1) * 1e3 / reps, total
 
 
 def measure(ctx, inst: Instance, f: np.ndarray):
-    """Times (us) of the cascade and of the 3-way join at every share scale."""
+    """Times (us) of the three plans (None: not run) and the join's total;
+    every plan that runs must give the same total."""
     rows_est = 2.0 ** float(f[8]) - 1.0
-    t = {}
+    t = [None, None, None]
     totals = set()
-    for k in SCALES:
-        t[("mw", k)], tot = time_plan(ctx, inst, False, k)
+    for p in (1, 2):
+        t[p], tot = time_plan(ctx, inst, p)
         totals.add(tot)
     if rows_est <= CASCADE_ROW_LIMIT:
-        t["cascade"], tot = time_plan(ctx, inst, True, rows_hint=rows_est)
+        t[0], tot = time_plan(ctx, inst, 0, rows_hint=rows_est)
         totals.add(tot)
-    else:
-        t["cascade"] = None
     if len(totals) != 1:
         raise AssertionError(f"plans disagree on the result: {sorted(totals)}")
     return t, totals.pop()
@@ -159,7 +163,7 @@ def measure(ctx, inst: Instance, f: np.ndarray):
 # the planner
 # ---------------------------------------------------------------------------
 class Planner:
-    """Normalisation + network; choose() returns (cascade?, share scale)."""
+    """Normalisation + network; choose() returns the plan index (0, 1, 2)."""
 
     def __init__(self, ctx, params=None, fmean=None, fstd=None, ymean=None, ystd=None):
         self.ctx = ctx
@@ -170,14 +174,14 @@ class Planner:
         self.ystd = np.ones(3, np.float32) if ystd is None else np.asarray(ystd, np.float32)
 
     def predict(self, F: np.ndarray) -> np.ndarray:
+        """Predicted log2 microseconds of the three plans, one row per instance."""
         import torch
         X = torch.from_numpy(((F - self.fmean) / self.fstd).astype(np.float32)).to(self.ctx.device)
         Y = self.mlp.forward(X).cpu().numpy()
         return Y * self.ystd + self.ymean
 
     def choose(self, F: np.ndarray):
-        P = self.predict(np.atleast_2d(F))
-        return [(bool(p[0] < p[1]), int(np.clip(np.rint(p[2]), -1, 1))) for p in P]
+        return [int(np.argmin(p)) for p in self.predict(np.atleast_2d(F))]
 
     def save(self, path):
         np.savez(path, params=self.mlp.get_params(), fmean=self.fmean, fstd=self.fstd,
@@ -193,56 +197,38 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "planner_weig
 
 
 def default_planner(ctx) -> Planner:
-    """The network trained on 20000 engine-timed instances (planner_weights.npz)."""
+    """The network trained on engine-timed instances (planner_weights.npz)."""
     return Planner.load(ctx, WEIGHTS)
+
+
+def cost_model_choice(F: np.ndarray, hbm_gbs=6792.1):
+    return [int(np.argmin(binding.cost_model(f, hbm_gbs))) for f in np.atleast_2d(F)]
 
 
 def plan_and_run(ctx, kind, R, S, T, mode="count", planner: Planner | None = None, **kw):
     """Choose a plan (the learned planner, else the cost model) and run it.
-    Returns (result, (cascade?, share scale))."""
+    Returns (result, plan index)."""
     F = features(ctx, kind, R, S, T)
     choice = (planner.choose(F) if planner is not None else cost_model_choice(F))[0]
-    return run_plan(ctx, kind, R, S, T, choice[0], choice[1], mode, **kw), choice
+    if choice == 0 and 2.0 ** float(F[8]) - 1.0 > CASCADE_ROW_LIMIT:
+        choice = 1   # the cascade would not fit its intermediate: the 3-way join instead
+    return run_plan(ctx, kind, R, S, T, choice, mode, **kw), choice
 
 
-def cost_model_choice(F: np.ndarray, hbm_gbs=6792.1):
-    out = []
-    for f in np.atleast_2d(F):
-        c = binding.cost_model(f, hbm_gbs)
-        out.append((bool(c[0] < c[1]), int(np.rint(c[2]))))
-    return out
-
-
-def labels(times, F, calib):
-    """Targets: log2 us of the cascade, of the 3-way join (scale 0), best scale."""
+def labels(times):
+    """Targets log2 us of the three plans; mask 0 where a plan was not run."""
     Y = np.zeros((len(times), 3), np.float32)
-    M = np.ones((len(times), 3), np.float32)
+    M = np.zeros((len(times), 3), np.float32)
     for i, t in enumerate(times):
-        tc = t["cascade"]
-        if tc is None:   # not run: the cost model's prediction, calibrated on the runs
-            tc = 2.0 ** (binding.cost_model(F[i])[0] + calib) * 1e6
-        Y[i, 0] = math.log2(tc)
-        Y[i, 1] = math.log2(t[("mw", 0)])
-        Y[i, 2] = min(SCALES, key=lambda k: t[("mw", k)])
+        for p in range(3):
+            if t[p] is not None:
+                Y[i, p] = math.log2(max(t[p], 1e-3))
+                M[i, p] = 1.0
     return Y, M
 
 
-def calibration(times, F):
-    d = [math.log2(t["cascade"] * 1e-6) - binding.cost_model(F[i])[0]
-         for i, t in enumerate(times) if t["cascade"] is not None]
-    return float(np.median(d)) if d else 0.0
-
-
-def plan_time(t, choice):
-    cascade, k = choice
-    if cascade:
-        return t["cascade"] if t["cascade"] is not None else float("inf")
-    return t[("mw", k)]
-
-
-def best_time(t):
-    c = [v for key, v in t.items() if v is not None]
-    return min(c)
+def plan_time(t, p):
+    return t[p] if t[p] is not None else float("inf")
 
 
 def train(planner: Planner, F, Y, M, steps=3000, batch=512, lr=1e-3, seed=0, log=None):
@@ -268,34 +254,57 @@ def train(planner: Planner, F, Y, M, steps=3000, batch=512, lr=1e-3, seed=0, log
     return losses
 
 
-def evaluate(planner: Planner, F, times):
-    """Regret t(plan)/t(best) - 1 of the learned planner, the cost model and
-    the plain cascade on instances whose plans were all timed."""
+def evaluate(planner: Planner, F, times, sizes=None):
+    """Regret t(plan) / t(best measured plan) - 1 of the learned planner, the
+    cost model alone, and each fixed plan, on instances whose 3-way plans
+    were all timed; and, where the intermediate |R join S| exceeds the inputs
+    |R| + |S| + |T|, the learned plan's speed-up over the plain cascade."""
     learned = planner.choose(F)
     model = cost_model_choice(F)
-    res = {"learned": [], "cost_model": [], "cascade": [], "multiway_default": []}
+    res = {"learned": [], "cost_model": [], "cascade": [], "default": [], "alt": []}
+    big_speedup, big_beats = [], []
     for i, t in enumerate(times):
-        b = best_time(t)
+        b = min(plan_time(t, p) for p in range(3))
         res["learned"].append(plan_time(t, learned[i]) / b - 1)
         res["cost_model"].append(plan_time(t, model[i]) / b - 1)
-        res["cascade"].append(plan_time(t, (True, 0)) / b - 1)
-        res["multiway_default"].append(plan_time(t, (False, 0)) / b - 1)
+        for p, name in enumerate(PLANS):
+            res[name].append(plan_time(t, p) / b - 1)
+        inputs = (sum(sizes[i]) if sizes is not None else
+                  sum(2.0 ** float(F[i][k]) - 1.0 for k in range(3)))
+        if 2.0 ** float(F[i][8]) - 1.0 > inputs:
+            tc = plan_time(t, 0)
+            tl = plan_time(t, learned[i])
+            big_speedup.append(tc / tl)
+            big_beats.append(tl < tc)
     summary = {}
     for k, v in res.items():
         a = np.array(v)
         fin = np.isfinite(a)
-        summary[k] = {"mean_regret": float(np.mean(np.where(fin, a, np.nan)[fin])) if fin.any() else None,
+        summary[k] = {"mean_regret": float(np.mean(a[fin])) if fin.any() else None,
                       "geo_mean_slowdown": float(np.exp(np.mean(np.log1p(a[fin])))) if fin.any() else None,
                       "within_10pct": float(np.mean(a <= 0.10)),
                       "not_runnable": int((~fin).sum())}
+    bs = np.array(big_speedup)
+    fin = np.isfinite(bs)
+    summary["intermediate_above_inputs"] = {
+        "instances": len(big_speedup),
+        "learned_beats_cascade": float(np.mean(big_beats)) if big_beats else None,
+        "geo_mean_speedup_over_cascade_runnable": float(np.exp(np.mean(np.log(bs[fin])))) if fin.any() else None,
+        "cascade_not_runnable": int((~fin).sum())}
+    summary["n"] = len(times)
     return summary, res
 
 
 # ---------------------------------------------------------------------------
 # data collection and the training run
 # ---------------------------------------------------------------------------
-def collect(ctx, n: int, seed: int, budget_s: float, log=None, **kw):
-    """Up to n timed instances (stops early when budget_s seconds are spent)."""
+def collect(ctx, n: int, seed: int, budget_s: float, log=None, keep_small: int = 0, **kw):
+    """Up to n timed instances (stops early when budget_s seconds are spent).
+    Returns features, times, totals, metadata and the count of instances
+    rejected (intermediate above REJECT_ROW_LIMIT, or a workspace the GPU
+    cannot hold).  With keep_small > 0 each metadata entry of an instance of
+    at most keep_small tuples in all also holds host copies of its relations
+    ("rel"), so that its total can be checked elsewhere."""
     import torch
     gen = torch.Generator(device=ctx.device)
     gen.manual_seed(seed)
@@ -316,32 +325,35 @@ def collect(ctx, n: int, seed: int, budget_s: float, log=None, **kw):
                 rejected += 1
                 continue
             raise
+        except torch.cuda.OutOfMemoryError:
+            ctx._ws = None
+            torch.cuda.empty_cache()
+            rejected += 1
+            continue
         F.append(f)
         times.append(t)
         totals.append(tot)
-        meta.append({"kind": int(inst.kind), "sizes": list(inst.sizes), "domains": list(inst.domains),
-                     "zipf": inst.zipf_s})
-        if log and len(F) % 500 == 0:
+        m = {"kind": int(inst.kind), "sizes": list(inst.sizes), "domains": list(inst.domains),
+             "zipf": inst.zipf_s}
+        if keep_small and sum(inst.sizes) <= keep_small:
+            m["rel"] = [tuple(c.cpu().numpy() for c in rel) for rel in (inst.R, inst.S, inst.T)]
+        meta.append(m)
+        if log and len(F) % 1000 == 0:
             log(f"{len(F)} instances, {time.time() - t0:.0f} s, rejected {rejected}")
     return np.array(F, np.float32), times, totals, meta, rejected
 
 
-def _times_to_arrays(times):
-    keys = ["cascade"] + [("mw", k) for k in SCALES]
-    A = np.full((len(times), len(keys)), np.nan)
+def _times_to_array(times):
+    A = np.full((len(times), 3), np.nan)
     for i, t in enumerate(times):
-        for j, k in enumerate(keys):
-            if t[k] is not None:
-                A[i, j] = t[k]
+        for p in range(3):
+            if t[p] is not None:
+                A[i, p] = t[p]
     return A
 
 
-def _arrays_to_times(A):
-    keys = ["cascade"] + [("mw", k) for k in SCALES]
-    out = []
-    for row in A:
-        out.append({k: (None if np.isnan(row[j]) else float(row[j])) for j, k in enumerate(keys)})
-    return out
+def _array_to_times(A):
+    return [[None if np.isnan(v) else float(v) for v in row] for row in A]
 
 
 def main():
@@ -350,13 +362,13 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--eval", type=int, default=512)
-    ap.add_argument("--budget", type=float, default=900.0, help="seconds for collecting training data")
-    ap.add_argument("--size-hi", type=int, default=1 << 22)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--budget", type=float, default=1200.0, help="seconds for collecting training data")
+    ap.add_argument("--size-hi", type=int, default=1 << 24)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--out", default="planner_run")
     ap.add_argument("--seed", type=int, default=1905)
     ap.add_argument("--eval-only", action="store_true",
-                    help="time the held-out instances on this engine and score the packaged weights")
+                    help="time held-out instances on this engine and score the packaged weights")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     log = lambda m: print(m, flush=True)
@@ -364,9 +376,9 @@ def main():
     ctx = binding.Context(0)
     t0 = time.time()
     if args.eval_only:
-        Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
-        summary, _ = evaluate(default_planner(ctx), Fev, tev)
-        rep = {"n_eval": len(Fev), "eval": summary, "collect_seconds": time.time() - t0,
+        Fev, tev, _, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
+        summary, _ = evaluate(default_planner(ctx), Fev, tev, [m["sizes"] for m in mev])
+        rep = {"n_eval": len(Fev), "rejected": rej2, "eval": summary, "collect_seconds": time.time() - t0,
                "weights": "packaged planner_weights.npz"}
         json.dump(rep, open(os.path.join(args.out, "report_eval.json"), "w"), indent=1)
         log(json.dumps(rep, indent=1))
@@ -374,17 +386,16 @@ def main():
     Ftr, ttr, _, mtr, rej = collect(ctx, args.train, args.seed, args.budget, log, size_hi=args.size_hi)
     log(f"train: {len(Ftr)} instances in {time.time() - t0:.0f} s ({rej} rejected)")
     Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
-    np.savez(os.path.join(args.out, "dataset.npz"), Ftrain=Ftr, Ttrain=_times_to_arrays(ttr),
-             Feval=Fev, Teval=_times_to_arrays(tev), totals_eval=np.array(totev, dtype=np.int64))
+    np.savez(os.path.join(args.out, "dataset.npz"), Ftrain=Ftr, Ttrain=_times_to_array(ttr),
+             Feval=Fev, Teval=_times_to_array(tev), totals_eval=np.array(totev, dtype=np.int64))
     json.dump({"train_meta": mtr, "eval_meta": mev}, open(os.path.join(args.out, "meta.json"), "w"))
-    calib = calibration(ttr, Ftr)
-    Y, M = labels(ttr, Ftr, calib)
+    Y, M = labels(ttr)
     planner = Planner(ctx, _init(args.seed))
     losses = train(planner, Ftr, Y, M, steps=args.steps, log=log)
     planner.save(os.path.join(args.out, "planner.npz"))
-    summary, _ = evaluate(planner, Fev, tev)
-    rep = {"n_train": len(Ftr), "n_eval": len(Fev), "calibration_log2": calib, "losses": losses,
-           "eval": summary, "collect_seconds": time.time() - t0}
+    summary, _ = evaluate(planner, Fev, tev, [m["sizes"] for m in mev])
+    rep = {"n_train": len(Ftr), "n_eval": len(Fev), "rejected_train": rej, "rejected_eval": rej2,
+           "size_hi": args.size_hi, "losses": losses, "eval": summary, "collect_seconds": time.time() - t0}
     json.dump(rep, open(os.path.join(args.out, "report.json"), "w"), indent=1)
     log(json.dumps(rep["eval"], indent=1))
 

@@ -94,3 +94,29 @@ def test_batched_workload_full_size_sampled(ctx):
     pick = np.unique(np.concatenate([np.argsort(-sizes)[:8], g.choice(len(qs), 40, replace=False)]))
     for i in pick:
         assert got[i] == oracle_count(qs[i]), i
+
+
+def test_autotuned_batch_is_exact(ctx):
+    """Rules tuned on the engine change the plans, never a count: every query
+    of a batch created after tuning gives the oracle's count, and restoring
+    the library's rules gives the same counts again."""
+    from paper_1905_13376_gb300 import autotune
+    qs = small_queries(200, 7)
+    dev = [(binding.MWJ_LINEAR if q.kind == "linear" else binding.MWJ_CYCLIC, cu(q.R), cu(q.S), cu(q.T))
+           for q in qs]
+    tuning = autotune.autotune(ctx, dev, sample=12, reps=2)
+    assert tuning["rules"] and len(tuning["launch"]) == 2
+    want = np.array([oracle_count(q) for q in qs], dtype=np.int64)
+    b = binding.Batch(ctx, dev)
+    assert np.array_equal(b.launch().cpu().numpy(), want)
+    # a rule far from the library's: a few R tuples per bucket, every cyclic tile small
+    ctx.batch_set_rules([(binding.MWJ_LINEAR, c, 64, 8, 0) for c in range(32)] +
+                        [(binding.MWJ_CYCLIC, c, 0, 0, 10) for c in range(32)])
+    ctx.batch_set_launch(1, 1)
+    b2 = binding.Batch(ctx, dev)
+    assert np.array_equal(b2.launch().cpu().numpy(), want)
+    assert any(b2.shares(i) != b.shares(i) for i in range(len(qs)))
+    ctx.batch_set_rules([])
+    ctx.batch_set_launch(0, 0)
+    b3 = binding.Batch(ctx, dev)
+    assert np.array_equal(b3.launch().cpu().numpy(), want)

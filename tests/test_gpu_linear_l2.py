@@ -125,6 +125,18 @@ def test_table_layouts(ctx, t_spread, w_spread):
     assert int(want["total"]) > (1 << 33)
 
 
+@pytest.mark.parametrize("n", [1023, 1024, 1025, 5000, 3 * 1024 * 152 + 13])
+def test_round_boundaries(ctx, n):
+    """Sizes around one CTA's 1024 tuples of warp rounds and a run of rounds
+    over every SM with a ragged tail, sorted by A and by B so that runs of
+    equal keys cross lanes, warps and CTAs."""
+    g = np.random.default_rng(n)
+    R = (np.sort(g.integers(0, 700, n)).astype(np.int32), g.integers(0, 900, n).astype(np.int32))
+    S = (np.sort(g.integers(0, 900, n)).astype(np.int32), g.integers(0, 800, n).astype(np.int32))
+    T = (g.integers(0, 800, n).astype(np.int32), g.integers(0, 5, n).astype(np.int32))
+    check(ctx, R, S, T, 700)
+
+
 def test_domain_error(ctx):
     R = (np.array([0, 5, 1], np.int32), np.array([1, 1, 2], np.int32))
     S = (np.array([1, 2], np.int32), np.array([2, 2], np.int32))

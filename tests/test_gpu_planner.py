@@ -144,27 +144,29 @@ def test_cost_model_orders_plans_by_intermediate_size(ctx):
 
 
 def test_trained_network_gains_over_cost_model(ctx):
-    """Train on engine-timed instances and compare plan regret on held-out
-    ones with the cost model alone (the planner without the network)."""
-    Ftr, ttr, _, _, _ = planner.collect(ctx, 500, 11, 120.0, size_hi=1 << 16)
-    Fev, tev, totev, mev, _ = planner.collect(ctx, 120, 12, 120.0, size_hi=1 << 16)
-    calib = planner.calibration(ttr, Ftr)
-    Y, M = planner.labels(ttr, Ftr, calib)
-    pl = planner.Planner(ctx, planner._init(13))
-    planner.train(pl, Ftr, Y, M, steps=1500, batch=256)
-    summary, _ = planner.evaluate(pl, Fev, tev)
-    learned = summary["learned"]["geo_mean_slowdown"]
-    model = summary["cost_model"]["geo_mean_slowdown"]
-    print("held-out geo-mean slowdown vs best plan: learned", learned, "cost model", model,
-          "plain cascade", summary["cascade"]["geo_mean_slowdown"])
-    assert learned <= model * 1.02
-    # every answer is exact whatever the plan: check the small ones against the oracle
+    """The packaged network (trained on engine timings of instances up to 2^24
+    tuples per relation) against the planner without it -- the cost model
+    alone -- on held-out instances the engine times now (a seed the training
+    never saw, up to 2^20 tuples per relation): a strictly smaller mean regret
+    against the best measured plan, and at least as many plans within 10 % of
+    it.  Every plan of every instance gave the same total (checked while
+    timing); the small instances' totals are checked against the oracle."""
+    pl = planner.default_planner(ctx)
+    F, times, totals, meta, _ = planner.collect(ctx, 160, 424242, 240.0, size_hi=1 << 20, keep_small=30000)
+    assert len(F) >= 100
+    summary, _ = planner.evaluate(pl, F, times, [m["sizes"] for m in meta])
+    learned, model = summary["learned"], summary["cost_model"]
+    print("held-out regret: learned", learned, "cost model", model, "default plan", summary["default"],
+          "cascade", summary["cascade"])
+    assert learned["mean_regret"] < model["mean_regret"]
+    assert learned["within_10pct"] >= model["within_10pct"]
     checked = 0
-    for i, m in enumerate(mev):
-        if sum(m["sizes"]) < 20000 and checked < 10:
-            checked += 1   # (the instances live on the GPU; exactness across plans is
-            #              asserted inside measure() for every instance)
-    assert checked >= 0
+    for m, tot in zip(meta, totals):
+        if "rel" in m:
+            fn = oracle.linear if m["kind"] == binding.MWJ_LINEAR else oracle.cyclic
+            assert tot == fn(*m["rel"])["total"]
+            checked += 1
+    assert checked >= 5
 
 
 def test_trained_planner_plans_are_exact(ctx):
@@ -174,8 +176,11 @@ def test_trained_planner_plans_are_exact(ctx):
     for kind in ["linear", "cyclic", "linear", "cyclic"]:
         q = datagen.random_query(g, kind, size_lo=500, size_hi=20000, dom_lo=50, dom_hi=5000)
         k = binding.MWJ_LINEAR if kind == "linear" else binding.MWJ_CYCLIC
-        res, choice = planner.plan_and_run(ctx, k, cu(q.R), cu(q.S), cu(q.T), planner=pl)
         fn = oracle.linear if kind == "linear" else oracle.cyclic
-        assert int(res["total"].item()) == fn(q.R, q.S, q.T)["total"], choice
+        want = fn(q.R, q.S, q.T)["total"]
+        res, choice = planner.plan_and_run(ctx, k, cu(q.R), cu(q.S), cu(q.T), planner=pl)
+        assert int(res["total"].item()) == want, choice
         res, _ = planner.plan_and_run(ctx, k, cu(q.R), cu(q.S), cu(q.T), planner=None)
-        assert int(res["total"].item()) == fn(q.R, q.S, q.T)["total"]
+        assert int(res["total"].item()) == want
+        for p in range(3):   # every plan the planner may choose
+            assert int(planner.run_plan(ctx, k, cu(q.R), cu(q.S), cu(q.T), p)["total"].item()) == want
