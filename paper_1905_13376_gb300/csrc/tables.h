@@ -66,7 +66,8 @@ cudaError_t tables_build(const uint32_t *keys, const uint2 *pairs, const uint32_
 
 // slots to reserve for the single table of nT tuples (worst case)
 size_t single_table_slots(int64_t nT);
-// ekey/ecnt: nT entries each; ecount: J; meta: 2.
+// ekey/ecnt: nT entries each; ecount: J; meta: at least 4 words (the layout
+// flag, kMetaDense, is written too).
 cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32_t J, uint32_t seed,
                                uint32_t *ekey, uint32_t *ecnt, uint32_t *ecount, uint32_t *meta,
                                uint64_t *tbl, DevStatus *status, int num_sms, cudaStream_t st);
@@ -74,7 +75,8 @@ cudaError_t single_table_build(const uint32_t *keys, const uint32_t *off, uint32
 // One table without partitioning T: a HyperLogLog pass over the keys sizes
 // the table (2^k >= 4 x the estimate, at most reserve_slots), then the keys
 // are inserted directly.  hll_regs: hll_scratch_registers(num_sms) u32 (per-CTA
-// registers, then the sizing step's partial sums); meta: 2 u32.
+// registers, then the sizing step's partial sums, then per-CTA key ranges);
+// meta: at least 4 u32, kMetaWords when allow_dense.
 // allow_dense: the keys may get the direct-address layout (meta words above);
 // meta must then hold kMetaWords words.
 cudaError_t single_table_direct(const int32_t *keys, int64_t n, uint32_t seed, unsigned int *hll_regs,

@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1905)
     ap.add_argument("--eval-only", action="store_true",
                     help="time held-out instances on this engine and score the packaged weights")
+    ap.add_argument("--from-dataset", default=None,
+                    help="train and score from a saved dataset.npz (+ meta.json beside it) without timing again")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     log = lambda m: print(m, flush=True)
@@ -383,12 +385,19 @@ def main():
         json.dump(rep, open(os.path.join(args.out, "report_eval.json"), "w"), indent=1)
         log(json.dumps(rep, indent=1))
         return
-    Ftr, ttr, _, mtr, rej = collect(ctx, args.train, args.seed, args.budget, log, size_hi=args.size_hi)
-    log(f"train: {len(Ftr)} instances in {time.time() - t0:.0f} s ({rej} rejected)")
-    Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
-    np.savez(os.path.join(args.out, "dataset.npz"), Ftrain=Ftr, Ttrain=_times_to_array(ttr),
-             Feval=Fev, Teval=_times_to_array(tev), totals_eval=np.array(totev, dtype=np.int64))
-    json.dump({"train_meta": mtr, "eval_meta": mev}, open(os.path.join(args.out, "meta.json"), "w"))
+    if args.from_dataset:
+        d = np.load(args.from_dataset)
+        meta = json.load(open(os.path.join(os.path.dirname(args.from_dataset), "meta.json")))
+        Ftr, ttr, Fev, tev = d["Ftrain"], _array_to_times(d["Ttrain"]), d["Feval"], _array_to_times(d["Teval"])
+        mtr, mev, rej, rej2 = meta["train_meta"], meta["eval_meta"], None, None
+        log(f"dataset {args.from_dataset}: {len(Ftr)} training and {len(Fev)} held-out instances")
+    else:
+        Ftr, ttr, _, mtr, rej = collect(ctx, args.train, args.seed, args.budget, log, size_hi=args.size_hi)
+        log(f"train: {len(Ftr)} instances in {time.time() - t0:.0f} s ({rej} rejected)")
+        Fev, tev, totev, mev, rej2 = collect(ctx, args.eval, args.seed + 1, 1e9, log, size_hi=args.size_hi)
+        np.savez(os.path.join(args.out, "dataset.npz"), Ftrain=Ftr, Ttrain=_times_to_array(ttr),
+                 Feval=Fev, Teval=_times_to_array(tev), totals_eval=np.array(totev, dtype=np.int64))
+        json.dump({"train_meta": mtr, "eval_meta": mev}, open(os.path.join(args.out, "meta.json"), "w"))
     Y, M = labels(ttr)
     planner = Planner(ctx, _init(args.seed))
     losses = train(planner, Ftr, Y, M, steps=args.steps, log=log)

@@ -68,3 +68,8 @@ def test_regret_against_the_best_measured_plan():
     assert big["instances"] == 2 and big["cascade_not_runnable"] == 1
     assert big["learned_beats_cascade"] == 1.0
     assert big["geo_mean_speedup_over_cascade_runnable"] == pytest.approx(100.0 / 25.0)
+
+
+def test_times_round_trip_through_the_saved_dataset():
+    times = [[None, 1.5, 2.0], [3.0, 4.0, None]]
+    assert planner._array_to_times(planner._times_to_array(times)) == times
