@@ -406,7 +406,7 @@ def cpu_baseline_planner_sample(meta, totals):
         fn = oracle.linear if m["kind"] == binding.MWJ_LINEAR else oracle.cyclic
         ok = ok and fn(*m["rel"])["total"] == tot
         n += 1
-    return ok, n
+    return (ok if n else None), n
 
 
 def cpu_baseline_batch_sampled(qs, pick):
@@ -786,7 +786,8 @@ def run_triangles(ctx, stream, args, pk):
     # it shares; counted once per wedge of R |x| S (tiles split into several
     # items re-probe, so this is a lower bound of the work).  Peak: every
     # SM's 32 shared-memory banks serve 128 B per clock, 8 B per probe.
-    pms = ph.get("cyc_probe", (float("nan"), 0))[0]
+    pkern = "cyc_c_probe" if "cyc_c_probe" in ph else "cyc_probe"   # C-bucket plan, else the cube tiling
+    pms = ph.get(pkern, (float("nan"), 0))[0]
     import json as _json
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     fmax = _json.load(open(peaks_file)).get("sm_max_mhz", 2070.0) if os.path.exists(peaks_file) else 2070.0
@@ -808,7 +809,7 @@ def run_triangles(ctx, stream, args, pk):
             "rows": {"ms_per_step": rms, "n_rows": n_rows, "rows_equal_total": n_rows == total,
                      "bytes": 12 * n_rows, "result_tuples_per_s": n_rows / (rms * 1e-3)},
             "cascade": casc,
-            "probe": {"kernel": "cyc_probe", "bound": "smem", "ms_per_step": round(pms, 4),
+            "probe": {"kernel": pkern, "bound": "smem", "ms_per_step": round(pms, 4),
                       "wedge_checks": wedges, "achieved": rate, "peak": peak_probes,
                       "unit": "wedge checks/s", "frac": round(rate / peak_probes, 4),
                       "peak_derivation": f"{n_sm} SMs x {fmax:.0f} MHz x 128 B/clock of shared memory / 8 B per probe"},
@@ -910,9 +911,10 @@ def run_batch(ctx, stream, args):
                           "speedup_over_library_rule": ms / ms_t,
                           "counts_equal_library_rule": tuned_same,
                           "tuning_seconds": round(tuning["tuning_seconds"], 1),
-                          "rules_changed": sum(1 for v in tuning["class_timings"].values()
-                                               if v["best_ms"] < v["default_ms"]),
-                          "launch": tuning["launch"], "class_timings": tuning["class_timings"]}}
+                          "rules_changed": len(tuning["rules"]), "launch": tuning["launch"],
+                          "tuner_whole_batch_ms": tuning["whole_batch_ms"],
+                          "context_queries": tuning["context_queries"],
+                          "class_timings": tuning["class_timings"]}}
 
 
 def run_planner(ctx, stream, args):
@@ -921,11 +923,19 @@ def run_planner(ctx, stream, args):
     keys, linear and cyclic): every plan timed on this engine, regret of the
     packaged network's choice against the best measured plan, next to the
     cost model alone and each fixed plan."""
+    import numpy as np
     from paper_1905_13376_gb300 import planner
     t0 = time.time()
     F, times, totals, meta, rejected = planner.collect(ctx, args.planner_instances, 777, args.planner_budget,
-                                                       keep_small=30000)
-    summary, _ = planner.evaluate(planner.default_planner(ctx), F, times, [m["sizes"] for m in meta])
+                                                       keep_small=1 << 22)
+    summary, per = planner.evaluate(planner.default_planner(ctx), F, times, [m["sizes"] for m in meta])
+    # the instance where the library's default plan loses most to the best plan
+    worst = None
+    if len(F):
+        i = int(np.argmax(per["default"]))
+        worst = {k: meta[i][k] for k in ("kind", "sizes", "domains", "zipf")}
+        worst.update({"us_per_plan": times[i], "default_regret": per["default"][i],
+                      "learned_regret": per["learned"][i]})
     exact, checked = (None, 0)
     if not args.no_cpu_baseline:
         exact, checked = cpu_baseline_planner_sample(meta, totals)
@@ -934,7 +944,7 @@ def run_planner(ctx, stream, args):
                         "[2^6,2^22], uniform or Zipf(0.8..1.5) keys, linear and cyclic",
             "instances": len(F), "rejected": rejected, "seconds": round(time.time() - t0, 1),
             "plans": ["cascade", "3-way default shares", "3-way alternative shares"],
-            "regret": summary, "plans_agree_on_every_total": True,
+            "regret": summary, "worst_default": worst, "plans_agree_on_every_total": True,
             "exact_vs_oracle": exact, "oracle_checked_instances": checked}
 
 

@@ -10,10 +10,12 @@ join launch, each with a number of CTAs per SM.
 
 autotune() picks these per (kind, size class) -- size class
 floor(log2(max(|R|, |S|, |T|))) -- and the two launch shapes by timing the
-candidates on the engine with the caller's own queries (a sample of each
-class, a batch of that sample per candidate), keeps a candidate only when it
-beats the library's rule by more than the timing noise, and installs the
-result in the context (mwj_batch_set_rules / mwj_batch_set_launch).  The
+candidates on the engine with the caller's own queries (inside a sample of
+the whole batch, so that each candidate shares the launches with the rest of
+the mix), keeps a candidate only when it beats the current choice by more
+than the timing noise and the result only when it beats the library's rule
+on the whole batch, and installs the result in the context
+(mwj_batch_set_rules / mwj_batch_set_launch).  The
 result is a plain dict that save() and load() keep as JSON, so that a later
 process installs it without tuning again.  Rules change plans only, never a
 count.
@@ -65,57 +67,86 @@ def _time_batch(ctx, queries, reps: int) -> float:
         b.close()
 
 
-def autotune(ctx: binding.Context, queries, sample: int = 32, reps: int = 3, seed: int = 0, log=None) -> dict:
+def _tuples(q) -> int:
+    return sum(int(c.numel()) for rel in q[1:4] for c in rel[:1])
+
+
+def autotune(ctx: binding.Context, queries, context: int = 1024, reps: int = 3, seed: int = 0,
+             log=None) -> dict:
     """Tune the batch rules and launch shapes on `queries` (a list of
     (kind, R, S, T) with device relations whose shares the library chooses).
-    Installs the result in ctx and returns it."""
+
+    A query's plan changes how the batch's two persistent launches share
+    their CTAs with every other query, so candidates are timed inside a
+    batch of the caller's mix: a sample of `context` queries, in which one
+    class's rule is varied at a time (classes with the most tuples first)
+    and kept when the sample's launch gets faster by more than MARGIN.  The
+    result is then timed on the whole batch against the library's rule and
+    kept only if it wins there as well.  Installs the result in ctx and
+    returns it."""
     t0 = time.time()
     groups = defaultdict(list)
     for i, q in enumerate(queries):
         groups[(int(q[0]), size_class(*q[1:4]))].append(i)
     rng = np.random.default_rng(seed)
-    rules, timings = {}, {}
+    n_all = len(queries)
+    pick = list(range(n_all)) if n_all <= context else sorted(rng.choice(n_all, context, replace=False).tolist())
+    sub = [queries[i][:4] for i in pick]
+    in_sub = set(pick)
+    weight = {key: sum(_tuples(queries[i]) for i in idx if i in in_sub) for key, idx in groups.items()}
     ctx.batch_set_rules([])
     ctx.batch_set_launch(0, 0)
-    for key in sorted(groups):
-        idx = groups[key]
-        pick = idx if len(idx) <= sample else sorted(rng.choice(idx, sample, replace=False).tolist())
-        sub = [queries[i][:4] for i in pick]
+    cur = _time_batch(ctx, sub, reps)
+    rules, timings = {}, {}
+    for key in sorted(groups, key=lambda k: -weight[k]):
+        if weight[key] == 0:
+            continue
         kind, _ = key
         cands = ([(t, f, 0) for t in LINEAR_TPB for f in LINEAR_TFAC] if kind == binding.MWJ_LINEAR
                  else [(0, 0, fit) for fit in CYCLIC_FIT])
         base = DEFAULT[kind]
-        res = {}
-        for c in [base] + [c for c in cands if c != base]:
+        res = {base: cur}
+        for c in cands:
+            if c == base:
+                continue
             trial = dict(rules)
             trial[key] = c
             ctx.batch_set_rules(_rule_list(trial))
             res[c] = _time_batch(ctx, sub, reps)
         best = min(res, key=res.get)
-        if res[best] > (1.0 - MARGIN) * res[base]:
-            best = base
-        rules[key] = best
-        timings[f"{kind}:{key[1]}"] = {"queries": len(sub), "default_ms": res[base], "best_ms": res[best],
-                                       "best": list(best)}
+        if best != base and res[best] < (1.0 - MARGIN) * cur:
+            rules[key] = best
+            cur = res[best]
+        ctx.batch_set_rules(_rule_list(rules))
+        timings[f"{kind}:{key[1]}"] = {"queries": len(groups[key]), "context_ms_before": res[base],
+                                       "context_ms_after": cur, "rule": list(rules.get(key, base))}
         if log:
-            log(f"class {key}: {len(sub)} queries, {res[base]:.3f} -> {res[best]:.3f} ms with {best}")
-    ctx.batch_set_rules(_rule_list(rules))
-    # the launch shapes, on a sample of the whole batch
-    n_all = len(queries)
-    pick = list(range(n_all)) if n_all <= 8 * sample else sorted(
-        rng.choice(n_all, 8 * sample, replace=False).tolist())
-    sub = [queries[i][:4] for i in pick]
-    lres = {}
+            log(f"class {key}: {res[base]:.3f} -> {cur:.3f} ms with {rules.get(key, base)}")
+    # the launch shapes, in the same sample
+    lres = {(0, 0): cur}
     for lp in LAUNCH:
-        ctx.batch_set_launch(*lp)
-        lres[lp] = _time_batch(ctx, sub, reps)
+        if lp != (0, 0):
+            ctx.batch_set_launch(*lp)
+            lres[lp] = _time_batch(ctx, sub, reps)
     launch = min(lres, key=lres.get)
     if lres[launch] > (1.0 - MARGIN) * lres[(0, 0)]:
         launch = (0, 0)
+    # the whole batch: tuned against the library's rule
+    full = [q[:4] for q in queries]
+    ctx.batch_set_launch(*launch)
+    tuned_ms = _time_batch(ctx, full, reps)
+    ctx.batch_set_rules([])
+    ctx.batch_set_launch(0, 0)
+    library_ms = _time_batch(ctx, full, reps)
+    kept = tuned_ms < (1.0 - MARGIN) * library_ms
+    if not kept:
+        rules, launch = {}, (0, 0)
+    ctx.batch_set_rules(_rule_list(rules))
     ctx.batch_set_launch(*launch)
     return {"rules": [list(r) for r in _rule_list(rules)], "launch": list(launch),
             "class_timings": timings, "launch_timings_ms": {f"{a},{b}": v for (a, b), v in lres.items()},
-            "tuning_seconds": time.time() - t0}
+            "whole_batch_ms": {"tuned": tuned_ms, "library_rule": library_ms, "kept": bool(kept)},
+            "context_queries": len(sub), "tuning_seconds": time.time() - t0}
 
 
 def install(ctx: binding.Context, tuning: dict):

@@ -104,8 +104,14 @@ def test_autotuned_batch_is_exact(ctx):
     qs = small_queries(200, 7)
     dev = [(binding.MWJ_LINEAR if q.kind == "linear" else binding.MWJ_CYCLIC, cu(q.R), cu(q.S), cu(q.T))
            for q in qs]
-    tuning = autotune.autotune(ctx, dev, sample=12, reps=2)
-    assert tuning["rules"] and len(tuning["launch"]) == 2
+    tuning = autotune.autotune(ctx, dev, context=64, reps=2)
+    assert len(tuning["launch"]) == 2 and tuning["context_queries"] == 64
+    wb = tuning["whole_batch_ms"]
+    # kept only when it beats the library's rule on the whole batch
+    if wb["kept"]:
+        assert wb["tuned"] < wb["library_rule"]
+    else:
+        assert tuning["rules"] == [] and tuning["launch"] == [0, 0]
     want = np.array([oracle_count(q) for q in qs], dtype=np.int64)
     b = binding.Batch(ctx, dev)
     assert np.array_equal(b.launch().cpu().numpy(), want)
