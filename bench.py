@@ -49,7 +49,7 @@ L2_NOTE = "every input column pair (262 MB) exceeds the 129 MB L2; no flush"
 TRAFFIC = {
     "part_scatter": {"bytes_per_step": 970_700_000, "digest": "a8955b800db65c70",
                      "sources": ["csrc/partition.cu", "csrc/common.cuh", "csrc/internal.h", "csrc/skew.h"]},
-    "w_build": {"bytes_per_step": None, "digest": "",
+    "w_build": {"bytes_per_step": 282_970_000, "digest": "31653c3bfe715b04",
                 "sources": ["csrc/linear_l2.cu", "csrc/linear_l2.h", "csrc/common.cuh", "csrc/internal.h",
                             "csrc/skew.h", "csrc/tables.h", "csrc/warp_runs.cuh"]},
 }
