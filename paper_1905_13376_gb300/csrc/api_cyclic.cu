@@ -38,7 +38,9 @@ struct CycCLayout {
     void *scan_tmp;
     unsigned int *counter;
     unsigned long long *big_slots, *big_off, *bigset;
-    uint32_t *big_neg;
+    uint32_t *bigcnt, *big_neg;
+    unsigned long long *rep_set;   // the probe CTAs' regions for chunks that repeat (c, a) pairs
+    uint32_t *rep_cnt;
     void *scan_tmp64b;
     unsigned long long *bucket_rows, *bucket_base;
     void *scan_tmp64;
@@ -67,6 +69,9 @@ size_t cyc_c_layout(Arena &A, uint32_t z, const mwj_rel &R, const mwj_rel &S, co
     L.big_slots = A.take<unsigned long long>(z + 1);
     L.big_off = A.take<unsigned long long>(z + 2);
     L.bigset = A.take<unsigned long long>(4 * (size_t)T.n + 16);
+    L.bigcnt = A.take<uint32_t>(4 * (size_t)T.n + 16);
+    L.rep_set = A.take<unsigned long long>(cyc_c_rep_slots(num_sms));
+    L.rep_cnt = A.take<uint32_t>(cyc_c_rep_slots(num_sms));
     L.big_neg = A.take<uint32_t>(z + 1);
     L.scan_tmp64b = A.take<char>(scan_scratch_bytes(z + 1));
     if (rows) {
@@ -268,6 +273,7 @@ extern "C" mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_r
         g.z = p.z;
         g.big_off = LC.big_off;
         g.bigset = LC.bigset;
+        g.bigcnt = LC.bigcnt;
         g.big_neg = LC.big_neg;
         g.seed = sd.slot2;
         g.a_domain = out->a_domain;
@@ -276,7 +282,7 @@ extern "C" mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_r
         g.st = ctx->status;
         e = cyc_c_run(g, LC.items, LC.scan_tmp, LC.counter, LC.big_slots, LC.scan_tmp64b, LC.bucket_rows,
                       LC.bucket_base, LC.scan_tmp64, rows ? out->rows : nullptr, rows ? out->capacity : 0,
-                      rows ? (long long *)out->n_rows : nullptr, ctx->dev.num_sms, st);
+                      rows ? (long long *)out->n_rows : nullptr, LC.rep_set, LC.rep_cnt, ctx->dev.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cyclic probe");
         return MWJ_OK;
     }

@@ -42,7 +42,8 @@ struct CycCArgs {
     const uint32_t *offT;       // z + 1
     uint32_t z;
     const unsigned long long *big_off;   // z + 1: big buckets' set regions (slots), scanned
-    const unsigned long long *bigset;    // the regions
+    const unsigned long long *bigset;    // the regions: one slot per distinct (c, a) pair
+    const uint32_t *bigcnt;              // the pairs' multiplicities, at the same indexes
     const uint32_t *big_neg;             // z: (-1, -1) pairs of a big bucket
     uint32_t seed;              // hash of the (c, a) sets
     int32_t a_domain;
@@ -53,6 +54,9 @@ struct CycCArgs {
 
 // T tuples a bucket's on-chip set holds (larger buckets keep theirs in the L2).
 uint32_t cyc_c_tcap();
+// Slots of the probe CTAs' regions for chunks that repeat (c, a) pairs (the
+// rep_set (u64) and rep_cnt (u32) arguments of cyc_c_run).
+size_t cyc_c_rep_slots(int num_sms);
 // Group R = (a, b) by b (sizing pass over R's B column first).  hll:
 // hll_scratch_registers(num_sms) u32; reserve: the entries the arrays hold;
 // a_domain > 0: every a must lie in [0, a_domain) (MWJ_ERR_DOMAIN).
@@ -60,12 +64,15 @@ cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const
                          uint64_t reserve, unsigned int *bump, int32_t a_domain, DevStatus *status, int num_sms,
                          cudaStream_t st);
 // items: z + 1 u32; big_slots: z u64 (scanned into g.big_off, z + 2 u64,
-// with scan_tmp64b); g.bigset: 4 |T| + 16 u64 slots; g.big_neg: z u32;
-// bucket_rows: z + 1 u64, bucket_base: z + 2 u64 (row output).
+// with scan_tmp64b); g.bigset: 4 |T| + 16 u64 slots, g.bigcnt as many u32;
+// g.big_neg: z u32;
+// bucket_rows: z + 1 u64, bucket_base: z + 2 u64 (row output); rep_set,
+// rep_cnt: cyc_c_rep_slots(num_sms) u64 and u32.
 cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsigned int *counter,
                       unsigned long long *big_slots, void *scan_tmp64b, unsigned long long *bucket_rows,
                       unsigned long long *bucket_base, void *scan_tmp64, int32_t *rows, long long capacity,
-                      long long *n_rows, int num_sms, cudaStream_t st);
+                      long long *n_rows, unsigned long long *rep_set, uint32_t *rep_cnt, int num_sms,
+                      cudaStream_t st);
 
 uint32_t cyc_rcap();
 uint32_t cyc_tcap();

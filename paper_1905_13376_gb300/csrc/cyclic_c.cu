@@ -40,13 +40,21 @@ __device__ __forceinline__ unsigned long long cpack(uint32_t c, uint32_t a) {
     return ((unsigned long long)c << 32) | a;
 }
 
-// An on-chip (c, a) multiset: CC_TSLOTS / 2 buckets of two 8-byte slots (16
-// bytes, one shared-memory load), one entry per T tuple.  An insert takes the
-// first free slot of its home bucket or of the buckets after it, so the
-// occupied slots of a bucket are a prefix and a lookup can stop at the first
-// bucket with a free slot: with the set at most half full that is nearly
-// always the home bucket.
+// An on-chip (c, a) set: CC_TSLOTS / 2 buckets of two 8-byte slots (16
+// bytes, one shared-memory load), one slot per distinct pair.  An insert
+// takes the first slot of its home bucket or of the buckets after it that is
+// free or holds its pair, so the occupied slots of a bucket are a prefix and
+// a lookup can stop at the first bucket with a free slot: with the set at
+// most half full that is nearly always the home bucket.  T is a bag: a chunk
+// that repeats a pair (rare) is rebuilt in the CTA's own region of the
+// workspace with a multiplicity per slot and looked up there like a big
+// bucket's set, so that the lookups of every other chunk stay as they are.
 constexpr uint32_t CC_NB = CC_TSLOTS / 2;
+constexpr int CC_MAX_CTAS_PER_SM = 2;   // probe CTAs per SM (shared memory); one region each
+// two probe CTAs per SM: each keeps below half of the SM's 228 KB of shared
+// memory less the 1 KB the hardware reserves per CTA and the static arrays
+static_assert(CC_TSLOTS * 8 + CC_QCAP * 16 + (CC_QCAP + 1) * 4 + 1024 <= 228 * 1024 / 2 - 1024,
+              "the probe's shared memory must leave room for two CTAs per SM");
 
 __device__ __forceinline__ uint32_t cbucket(uint32_t c, uint32_t a, uint32_t seed) {
     uint32_t h = (c ^ seed) * 0x9E3779B1u ^ a * 0x85EBCA6Bu;
@@ -56,19 +64,25 @@ __device__ __forceinline__ uint32_t cbucket(uint32_t c, uint32_t a, uint32_t see
     return h & (CC_NB - 1);
 }
 
-__device__ __forceinline__ bool cset_insert(unsigned long long *tk, unsigned long long key, uint32_t bk) {
+// 1: the pair took a free slot; 2: it was there already; 0: the set is full.
+__device__ __forceinline__ int cset_insert(unsigned long long *tk, unsigned long long key, uint32_t bk) {
     for (uint32_t it = 0; it < CC_NB; ++it) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             unsigned long long *p = tk + 2 * bk + q;
-            if (*p == kEmpty64 && atomicCAS(p, kEmpty64, key) == kEmpty64) return true;
+            unsigned long long v = *p;
+            if (v == kEmpty64) {
+                v = atomicCAS(p, kEmpty64, key);
+                if (v == kEmpty64) return 1;
+            }
+            if (v == key) return 2;
         }
         bk = (bk + 1) & (CC_NB - 1);
     }
-    return false;
+    return 0;
 }
 
-// multiplicity of key in the set (key != kEmpty64)
+// 1 when key is in the set, else 0 (key != kEmpty64)
 __device__ __forceinline__ uint32_t cset_count(const unsigned long long *tk, unsigned long long key, uint32_t bk) {
     uint32_t m = 0;
     for (uint32_t it = 0; it < CC_NB; ++it) {
@@ -186,13 +200,16 @@ __global__ void k_cc_plan(const uint32_t *__restrict__ offS, const uint32_t *__r
     }
 }
 
-// Empty every big bucket's region (the total is the scan's last entry).
-__global__ void k_cc_bigclear(unsigned long long *__restrict__ gs, const unsigned long long *__restrict__ big_off,
-                              uint32_t z) {
+// Empty every big bucket's region and zero its counts (the total is the
+// scan's last entry).
+__global__ void k_cc_bigclear(unsigned long long *__restrict__ gs, uint32_t *__restrict__ gc,
+                              const unsigned long long *__restrict__ big_off, uint32_t z) {
     const unsigned long long total = big_off[z];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (unsigned long long)gridDim.x * blockDim.x)
+         i += (unsigned long long)gridDim.x * blockDim.x) {
         gs[i] = kEmpty64;
+        gc[i] = 0u;
+    }
 }
 
 __device__ __forceinline__ uint32_t gslot(uint32_t c, uint32_t a, uint32_t seed) {
@@ -204,11 +221,13 @@ __device__ __forceinline__ uint32_t gslot(uint32_t c, uint32_t a, uint32_t seed)
 }
 
 // Big buckets' sets: a CTA per bucket (buckets blockIdx.x, + gridDim.x, ...)
-// inserts T_k's (c, a) pairs into the bucket's region, one entry per tuple
-// (linear probing from gslot); (-1, -1) pairs are counted in big_neg[k].
+// inserts T_k's (c, a) pairs into the bucket's region, one slot per distinct
+// pair (linear probing from gslot) and its multiplicity in gc at the same
+// index; (-1, -1) pairs are counted in big_neg[k].
 __global__ void k_cc_bigbuild(const uint2 *__restrict__ Tp, const uint32_t *__restrict__ offT, uint32_t z,
                               const unsigned long long *__restrict__ big_off, unsigned long long *__restrict__ gs,
-                              uint32_t *__restrict__ big_neg, uint32_t seed, DevStatus *st) {
+                              uint32_t *__restrict__ gc, uint32_t *__restrict__ big_neg, uint32_t seed,
+                              DevStatus *st) {
     __shared__ uint32_t negs;
     for (uint32_t k = blockIdx.x; k < z; k += gridDim.x) {
         const unsigned long long base = big_off[k], slots = big_off[k + 1] - base;
@@ -217,6 +236,7 @@ __global__ void k_cc_bigbuild(const uint2 *__restrict__ Tp, const uint32_t *__re
         __syncthreads();
         const uint32_t mask = (uint32_t)(slots - 1);
         unsigned long long *reg = gs + base;
+        uint32_t *cnt = gc + base;
         for (uint32_t q = offT[k] + threadIdx.x; q < offT[k + 1]; q += blockDim.x) {
             const uint2 tu = __ldg(Tp + q);
             const unsigned long long key = cpack(tu.x, tu.y);
@@ -227,7 +247,10 @@ __global__ void k_cc_bigbuild(const uint2 *__restrict__ Tp, const uint32_t *__re
             uint32_t s = gslot(tu.x, tu.y, seed) & mask;
             bool done = false;
             for (uint32_t it = 0; it <= mask; ++it) {
-                if (reg[s] == kEmpty64 && atomicCAS(reg + s, kEmpty64, key) == kEmpty64) {
+                unsigned long long v = reg[s];
+                if (v == kEmpty64) v = atomicCAS(reg + s, kEmpty64, key);   // kEmpty64: claimed here
+                if (v == kEmpty64 || v == key) {
+                    atomicAdd(cnt + s, 1u);
                     done = true;
                     break;
                 }
@@ -246,15 +269,20 @@ __global__ void k_cc_bigbuild(const uint2 *__restrict__ Tp, const uint32_t *__re
 // item's count to its bucket's total); PASS 1 writes rows at positions taken
 // from the bucket's cursor (its scanned total, advanced atomically).
 template <int PASS>
-__global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t *__restrict__ item_off,
+__global__ void __launch_bounds__(CC_T, CC_MAX_CTAS_PER_SM) k_cc_probe(CycCArgs g, const uint32_t *__restrict__ item_off,
                                                       unsigned int *__restrict__ counter,
                                                       unsigned long long *__restrict__ bucket_rows,
-                                                      int32_t *__restrict__ rows, long long capacity) {
+                                                      int32_t *__restrict__ rows, long long capacity,
+                                                      unsigned long long *__restrict__ rep_set,
+                                                      uint32_t *__restrict__ rep_cnt) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *tk = (unsigned long long *)smraw;                      // CC_TSLOTS
     uint4 *queue = (uint4 *)(tk + CC_TSLOTS);                                   // CC_QCAP x (b, c, start, n)
     uint32_t *cpre = (uint32_t *)(queue + CC_QCAP);                             // CC_QCAP + 1 chunk offsets
-    __shared__ uint32_t item_s, tneg, batch_ctr, chunk_ctr, qn, carry;
+    __shared__ uint32_t item_s, tneg, batch_ctr, chunk_ctr, qn, carry, tdup;
+    // this CTA's region for a chunk that repeats pairs
+    unsigned long long *const my_set = rep_set + (size_t)blockIdx.x * CC_TSLOTS;
+    uint32_t *const my_cnt = rep_cnt + (size_t)blockIdx.x * CC_TSLOTS;
     __shared__ uint32_t scan_scratch[33];
     __shared__ unsigned long long red[32];
     const uint32_t z = g.z;
@@ -278,17 +306,19 @@ __global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t
         const uint32_t s0 = g.offS[k], s1 = g.offS[k + 1];
         // T_k's set: the item's chunk on chip, or for a big bucket its region
         // of the workspace, built before this kernel
-        const bool big = cc_big(g.offT[k + 1] - g.offT[k]);
+        bool big = cc_big(g.offT[k + 1] - g.offT[k]);
         const uint32_t ta = g.offT[k] + (item - item_off[k]) * CC_TCAP;
         const uint32_t tz = big ? g.offT[k + 1] : min(g.offT[k + 1], ta + CC_TCAP);
         const unsigned long long gbase = g.big_off[k];
-        const uint32_t gmask = (uint32_t)(g.big_off[k + 1] - gbase) - 1u;
+        uint32_t gmask = (uint32_t)(g.big_off[k + 1] - gbase) - 1u;
         const unsigned long long *gset = g.bigset + gbase;
+        const uint32_t *gcnt = g.bigcnt + gbase;
 
-        // ---- T_k as a (c, a) multiset: one entry per tuple ----
+        // ---- T_k as a (c, a) multiset: a slot per distinct pair ----
         if (!big)
             for (uint32_t q = threadIdx.x; q < CC_TSLOTS; q += CC_T) tk[q] = kEmpty64;
         if (threadIdx.x == 0) {
+            tdup = 0u;
             tneg = big ? g.big_neg[k] : 0u;
             batch_ctr = 0u;
             chunk_ctr = 0u;
@@ -303,9 +333,39 @@ __global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t
                 atomicAdd(&tneg, 1u);
                 continue;
             }
-            if (!cset_insert(tk, key, cbucket(tu.x, tu.y, g.seed))) set_status(g.st, MWJ_ERR_CHECK, 24);
+            const int r = cset_insert(tk, key, cbucket(tu.x, tu.y, g.seed));
+            if (r == 2 && !tdup) tdup = 1u;
+            if (r == 0) set_status(g.st, MWJ_ERR_CHECK, 24);
         }
         __syncthreads();
+        if (tdup) {
+            // the chunk repeats pairs: its set with multiplicities in this
+            // CTA's region, looked up through the L2 like a big bucket's
+            for (uint32_t q = threadIdx.x; q < CC_TSLOTS; q += CC_T) {
+                my_set[q] = kEmpty64;
+                my_cnt[q] = 0u;
+            }
+            __syncthreads();
+            for (uint32_t q = ta + threadIdx.x; q < tz; q += CC_T) {
+                const uint2 tu = __ldg(g.Tp + q);
+                const unsigned long long key = cpack(tu.x, tu.y);
+                if (key == kEmpty64) continue;   // counted in tneg already
+                uint32_t s = gslot(tu.x, tu.y, g.seed) & (CC_TSLOTS - 1);
+                for (uint32_t it = 0; it < CC_TSLOTS; ++it) {
+                    const unsigned long long v = atomicCAS(my_set + s, kEmpty64, key);
+                    if (v == kEmpty64 || v == key) {
+                        atomicAdd(my_cnt + s, 1u);
+                        break;
+                    }
+                    s = (s + 1) & (CC_TSLOTS - 1);
+                }
+            }
+            __syncthreads();
+            big = true;
+            gset = my_set;
+            gcnt = my_cnt;
+            gmask = CC_TSLOTS - 1;
+        }
         const uint32_t negs = tneg;
 
         // ---- stream S_k past the set ----
@@ -347,14 +407,16 @@ __global__ void __launch_bounds__(CC_T, 2) k_cc_probe(CycCArgs g, const uint32_t
             const unsigned long long key = cpack(c, a);
             if (key == kEmpty64) return negs;
             if (!big) return cset_count(tk, key, cbucket(c, a, g.seed));
-            uint32_t m = 0, s = gslot(c, a, g.seed) & gmask;
+            // a big bucket's set, or this CTA's for a chunk that repeats
+            // pairs (written in this kernel: read through the L2)
+            uint32_t s = gslot(c, a, g.seed) & gmask;
             for (uint32_t it = 0; it <= gmask; ++it) {
-                const unsigned long long v = __ldg(gset + s);
+                const unsigned long long v = __ldcg(gset + s);
+                if (v == key) return __ldcg(gcnt + s);
                 if (v == kEmpty64) break;
-                m += (v == key);
                 s = (s + 1) & gmask;
             }
-            return m;
+            return 0u;
         };
         // walk one list of the warp's: entries [lo, hi) of (b, c)'s R list,
         // 32 a step, two steps in flight
@@ -498,6 +560,8 @@ __global__ void k_cc_rows_check(const unsigned long long *base, uint32_t z, long
 
 }  // namespace
 
+size_t cyc_c_rep_slots(int num_sms) { return (size_t)num_sms * CC_MAX_CTAS_PER_SM * CC_TSLOTS; }
+
 uint32_t cyc_c_tcap() { return CC_TCAP; }
 
 cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const RGroup &r, unsigned int *hll,
@@ -530,7 +594,8 @@ cudaError_t rgroup_build(const int32_t *Ra, const int32_t *Rb, int64_t nR, const
 cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsigned int *counter,
                       unsigned long long *big_slots, void *scan_tmp64b, unsigned long long *bucket_rows,
                       unsigned long long *bucket_base, void *scan_tmp64, int32_t *rows, long long capacity,
-                      long long *n_rows, int num_sms, cudaStream_t st) {
+                      long long *n_rows, unsigned long long *rep_set, uint32_t *rep_cnt, int num_sms,
+                      cudaStream_t st) {
     const uint32_t z = g.z;
     const bool with_rows = (n_rows != nullptr);
     cudaError_t e;
@@ -547,12 +612,13 @@ cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsign
         return e;
     {
         ProfScope ps_("cyc_c_bigclear", st);
-        k_cc_bigclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)g.bigset, g.big_off, z);
+        k_cc_bigclear<<<num_sms * 4, 512, 0, st>>>((unsigned long long *)g.bigset, (uint32_t *)g.bigcnt,
+                                                   g.big_off, z);
     }
     {
         ProfScope ps_("cyc_c_bigbuild", st);
         k_cc_bigbuild<<<num_sms * 2, 512, 0, st>>>(g.Tp, g.offT, z, g.big_off, (unsigned long long *)g.bigset,
-                                                   (uint32_t *)g.big_neg, g.seed, g.st);
+                                                   (uint32_t *)g.bigcnt, (uint32_t *)g.big_neg, g.seed, g.st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = CC_TSLOTS * sizeof(unsigned long long) + CC_QCAP * sizeof(uint4) +
@@ -566,6 +632,7 @@ cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsign
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cc_probe<0>, CC_T, smem) != cudaSuccess || occ < 1)
         occ = 1;
+    if (occ > CC_MAX_CTAS_PER_SM) occ = CC_MAX_CTAS_PER_SM;   // one region per CTA for repeated pairs
     const unsigned grid = (unsigned)(num_sms * occ);
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     if (with_rows &&
@@ -573,7 +640,8 @@ cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsign
         return e;
     {
         ProfScope ps_("cyc_c_probe", st);
-        k_cc_probe<0><<<grid, CC_T, smem, st>>>(g, items, counter, with_rows ? bucket_rows : nullptr, nullptr, 0);
+        k_cc_probe<0><<<grid, CC_T, smem, st>>>(g, items, counter, with_rows ? bucket_rows : nullptr, nullptr, 0,
+                                                rep_set, rep_cnt);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!with_rows) return cudaSuccess;
@@ -586,7 +654,7 @@ cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsign
     }
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     ProfScope ps_("cyc_c_rows", st);
-    k_cc_probe<1><<<grid, CC_T, smem, st>>>(g, items, counter, bucket_base, rows, capacity);
+    k_cc_probe<1><<<grid, CC_T, smem, st>>>(g, items, counter, bucket_base, rows, capacity, rep_set, rep_cnt);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,37 @@ def test_c_buckets_hashed_b_keys_and_chunks(ctx):
         check_all_modes(ctx, R, S, T, 400, shares=shares, rows=False)
 
 
+@pytest.mark.parametrize("copies", [3, 4095, 4097, 70000])
+def test_c_buckets_repeated_pairs(ctx, copies):
+    """T holds one (c, a) pair many times (a bag): within one on-chip chunk,
+    split across a bucket's chunks, and in a big bucket's L2 set.  Each
+    distinct pair takes one slot with its multiplicity; every wedge it
+    closes counts (and is written) that many times."""
+    g = np.random.default_rng(copies)
+    T = (np.concatenate([np.full(copies, 9, np.int32), g.integers(0, 50, 3000).astype(np.int32)]),
+         np.concatenate([np.full(copies, 3, np.int32), g.integers(0, 40, 3000).astype(np.int32)]))
+    R = (np.concatenate([np.full(5, 3, np.int32), g.integers(0, 40, 2000).astype(np.int32)]),
+         np.concatenate([np.arange(5, dtype=np.int32), g.integers(0, 30, 2000).astype(np.int32)]))
+    S = (np.concatenate([np.arange(5, dtype=np.int32), g.integers(0, 30, 2000).astype(np.int32)]),
+         np.concatenate([np.full(5, 9, np.int32), g.integers(0, 50, 2000).astype(np.int32)]))
+    want = oracle.cyclic(R, S, T)["total"]
+    assert want >= 5 * copies
+    for shares in [None, (1, 1, 1), (1, 1, 4)]:
+        check_all_modes(ctx, R, S, T, 40, shares=shares)
+
+
+def test_c_buckets_tiny_a_domain_zipf_c(ctx):
+    """A large T over a tiny A domain with a Zipf C column: T's busiest C
+    values repeat each (c, a) pair thousands of times, in big buckets' L2
+    sets and in on-chip chunks alike.  Exact, in the time of its wedges."""
+    g = np.random.default_rng(71)
+    nR, nS, nT = 16597, 231622, 1 << 21
+    R = (g.integers(0, 71, nR).astype(np.int32), datagen._keys(g, nR, 43767, True, 1.07))
+    S = (datagen._keys(g, nS, 43767, True, 1.07), datagen._keys(g, nS, 400000, True, 1.07))
+    T = (datagen._keys(g, nT, 400000, True, 1.07), g.integers(0, 71, nT).astype(np.int32))
+    check_all_modes(ctx, R, S, T, 71, rows=False)
+
+
 def test_big_tiles_split_into_items(ctx):
     # one tile (shares 1,1,1) with R and T far above a chunk: many work items
     g = np.random.default_rng(4)
