@@ -384,6 +384,7 @@ namespace {
 
 constexpr int HLL_BITS = 12;
 constexpr uint32_t HLL_M = 1u << HLL_BITS;
+constexpr int HLL_CTAS_PER_SM = 2;   // resident CTAs of the sizing pass (its registers allow two)
 
 // HyperLogLog registers (Flajolet, Fusy, Gandouet, Meunier 2007): register
 // h >> (32 - HLL_BITS) keeps the largest rank (position of the first 1 bit)
@@ -391,7 +392,7 @@ constexpr uint32_t HLL_M = 1u << HLL_BITS;
 // keys have distinct hashes.
 // With mm != null the CTA also leaves the smallest and largest key it saw in
 // mm[2 b], mm[2 b + 1] (b = blockIdx.x; INT32_MAX, INT32_MIN when it saw none).
-__global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, uint32_t n,
+__global__ void __launch_bounds__(BT, HLL_CTAS_PER_SM) k_hll(const int32_t *__restrict__ keys, uint32_t n,
                                             uint32_t seed, unsigned int *__restrict__ regs,
                                             unsigned int *__restrict__ done, int32_t *__restrict__ mm) {
     __shared__ unsigned int r[HLL_M];
@@ -407,15 +408,16 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
     const bool vec = ((uintptr_t)keys & 15) == 0;
     const uint64_t pol = l2_evict_first();
     // strips of 16 consecutive keys, one per thread and iteration (four
-    // 16-byte loads in flight), so that a run of equal keys (edge lists come
-    // sorted by source) costs one register update per strip: a register only
-    // grows, so a key equal to its predecessor changes nothing
+    // 16-byte loads), so that a run of equal keys (edge lists come sorted by
+    // source) costs one register update per strip: a register only grows, so
+    // a key equal to its predecessor changes nothing.  The next strip's loads
+    // are issued before this one is used.
     const uint32_t nst = (n + 15) / 16;
     const uint32_t T = gridDim.x * BT;
-    for (uint32_t c = blockIdx.x * BT + threadIdx.x; c < nst; c += T) {
+    auto load = [&](uint32_t c, int32_t (&v)[16]) -> uint32_t {
+        if (c >= nst) return 0u;
         const uint32_t i = c * 16;
         const uint32_t cnt = min(16u, n - i);
-        int32_t v[16];
         if (cnt == 16 && vec) {
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
@@ -426,6 +428,14 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] = ((uint32_t)k < cnt) ? __ldg(keys + i + k) : 0;
         }
+        return cnt;
+    };
+    int32_t v[16];
+    uint32_t c = blockIdx.x * BT + threadIdx.x;
+    uint32_t cnt = load(c, v);
+    for (; c < nst; c += T) {
+        int32_t nv[16];
+        const uint32_t ncnt = load(c + T, nv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             if ((uint32_t)k >= cnt) break;
@@ -438,6 +448,9 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
             unsigned int *reg = &r[h >> (32 - HLL_BITS)];
             if (*(volatile unsigned int *)reg < rank) atomicMax(reg, rank);
         }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = nv[k];
+        cnt = ncnt;
     }
     if (mm) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -457,8 +470,6 @@ __global__ void __launch_bounds__(BT) k_hll(const int32_t *__restrict__ keys, ui
         mm[2 * blockIdx.x + 1] = smax;
     }
 }
-
-constexpr int HLL_CTAS_PER_SM = 3;
 
 // regs[0..HLL_M) = max over the rows of regs[ctas][HLL_M]
 __global__ void k_hll_merge(unsigned int *__restrict__ regs, uint32_t ctas) {
@@ -485,12 +496,14 @@ constexpr size_t HLL_TAIL = 2 * HLL_MCTAS + HLL_MCTAS + 8;
 // when their span max - min + 1 is at most the hashed table's slot count:
 // the keys then fill at least 1/(2 factor) of the span, the array is no
 // larger than the hashed table and a lookup is one load with no probing.
-__global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict__ regs, uint32_t rows,
+constexpr int HLL_MW = 32;   // warps of a merge CTA, each over every HLL_MW-th row
+
+__global__ void __launch_bounds__(HLL_MW * 32) k_hll_merge_size(unsigned int *__restrict__ regs, uint32_t rows,
                                                         unsigned int *__restrict__ tail, uint64_t reserve,
                                                         double factor, uint32_t *__restrict__ meta,
                                                         const int32_t *__restrict__ kr,
                                                         uint32_t *__restrict__ meta2, uint64_t reserve2) {
-    __shared__ unsigned int m[8][HLL_MB];
+    __shared__ unsigned int m[HLL_MW][HLL_MB];
     __shared__ bool last;
     double *part_s = (double *)tail;
     unsigned int *part_z = tail + 2 * HLL_MCTAS;
@@ -500,19 +513,19 @@ __global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict
     // eight rows in flight per thread: the rows are independent loads
     unsigned int mx = 0;
     uint32_t r = w;
-    for (; r + 56 < rows; r += 64) {
+    for (; r + 7 * HLL_MW < rows; r += 8 * HLL_MW) {
         unsigned int v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(regs + (size_t)(r + 8 * u) * HLL_M + j);
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(regs + (size_t)(r + HLL_MW * u) * HLL_M + j);
 #pragma unroll
         for (int u = 0; u < 8; ++u) mx = max(mx, v[u]);
     }
-    for (; r < rows; r += 8) mx = max(mx, __ldcg(regs + (size_t)r * HLL_M + j));
+    for (; r < rows; r += HLL_MW) mx = max(mx, __ldcg(regs + (size_t)r * HLL_M + j));
     m[w][lane] = mx;
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-        for (int q = 1; q < 8; ++q) mx = max(mx, m[q][lane]);
+        for (int q = 1; q < HLL_MW; ++q) mx = max(mx, m[q][lane]);
         regs[j] = mx;
         double sum = 1.0 / (double)(1ull << mx);   // exact: ranks are at most 33 - HLL_BITS
         unsigned int z = (mx == 0);
@@ -532,7 +545,7 @@ __global__ void __launch_bounds__(256) k_hll_merge_size(unsigned int *__restrict
     __threadfence();
     // the last CTA: the parts in a fixed order (lane l adds parts l, l + 32,
     // ... in turn, then a fixed butterfly), and the key ranges with all threads
-    __shared__ int32_t rlo[8], rhi[8];
+    __shared__ int32_t rlo[HLL_MW], rhi[HLL_MW];
     double S = 0.0;
     unsigned int Z = 0;
     if (w == 0) {
@@ -682,8 +695,8 @@ cudaError_t single_table_size(const int32_t *keys, int64_t n, uint32_t seed, uns
         if ((e = cudaMemsetAsync(done, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     }
     ProfScope ps_(size_name, st);
-    k_hll_merge_size<<<HLL_MCTAS, 256, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor, meta,
-                                                 mm, meta2, reserve2);
+    k_hll_merge_size<<<HLL_MCTAS, HLL_MW * 32, 0, st>>>(hll_regs, rows, tail, reserve_slots, kSingleTableFactor,
+                                                         meta, mm, meta2, reserve2);
     return cudaGetLastError();
 }
 
