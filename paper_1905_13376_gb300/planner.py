@@ -205,13 +205,19 @@ def cost_model_choice(F: np.ndarray, hbm_gbs=6792.1):
     return [int(np.argmin(binding.cost_model(f, hbm_gbs))) for f in np.atleast_2d(F)]
 
 
+def runnable(choice: int, f: np.ndarray) -> int:
+    """The plan that runs for a choice: the 3-way join with the default shares
+    instead of a cascade whose estimated intermediate would not fit."""
+    if choice == 0 and 2.0 ** float(f[8]) - 1.0 > CASCADE_ROW_LIMIT:
+        return 1
+    return choice
+
+
 def plan_and_run(ctx, kind, R, S, T, mode="count", planner: Planner | None = None, **kw):
     """Choose a plan (the learned planner, else the cost model) and run it.
     Returns (result, plan index)."""
     F = features(ctx, kind, R, S, T)
-    choice = (planner.choose(F) if planner is not None else cost_model_choice(F))[0]
-    if choice == 0 and 2.0 ** float(F[8]) - 1.0 > CASCADE_ROW_LIMIT:
-        choice = 1   # the cascade would not fit its intermediate: the 3-way join instead
+    choice = runnable((planner.choose(F) if planner is not None else cost_model_choice(F))[0], F)
     return run_plan(ctx, kind, R, S, T, choice, mode, **kw), choice
 
 
@@ -256,11 +262,12 @@ def train(planner: Planner, F, Y, M, steps=3000, batch=512, lr=1e-3, seed=0, log
 
 def evaluate(planner: Planner, F, times, sizes=None):
     """Regret t(plan) / t(best measured plan) - 1 of the learned planner, the
-    cost model alone, and each fixed plan, on instances whose 3-way plans
-    were all timed; and, where the intermediate |R join S| exceeds the inputs
-    |R| + |S| + |T|, the learned plan's speed-up over the plain cascade."""
-    learned = planner.choose(F)
-    model = cost_model_choice(F)
+    cost model alone (each choice as plan_and_run runs it), and each fixed
+    plan, on instances whose 3-way plans were all timed; and, where the
+    intermediate |R join S| exceeds the inputs |R| + |S| + |T|, the learned
+    plan's speed-up over the plain cascade."""
+    learned = [runnable(c, f) for c, f in zip(planner.choose(F), np.atleast_2d(F))]
+    model = [runnable(c, f) for c, f in zip(cost_model_choice(F), np.atleast_2d(F))]
     res = {"learned": [], "cost_model": [], "cascade": [], "default": [], "alt": []}
     big_speedup, big_beats = [], []
     for i, t in enumerate(times):

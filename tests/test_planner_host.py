@@ -73,3 +73,15 @@ def test_regret_against_the_best_measured_plan():
 def test_times_round_trip_through_the_saved_dataset():
     times = [[None, 1.5, 2.0], [3.0, 4.0, None]]
     assert planner._array_to_times(planner._times_to_array(times)) == times
+
+
+def test_a_cascade_too_large_runs_as_the_3way_join():
+    """A choice of the cascade whose estimated intermediate (feature 8 =
+    log2(|R join S| + 1)) is above the limit runs as the 3-way join with the
+    default shares, in plan_and_run and in the evaluation alike."""
+    f = np.zeros(24, np.float32)
+    f[8] = 31.0
+    assert planner.runnable(0, f) == 1
+    f[8] = 20.0
+    assert planner.runnable(0, f) == 0
+    assert planner.runnable(2, f) == 2 and planner.runnable(1, f) == 1
