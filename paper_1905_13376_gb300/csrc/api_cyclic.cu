@@ -271,6 +271,7 @@ extern "C" mwj_status mwj_join3_cyclic(mwj_ctx *ctx, mwj_rel R, mwj_rel S, mwj_r
         g.r = LC.r;
         g.Sp = LC.Sp; g.offS = LC.offS; g.Tp = LC.Tp; g.offT = LC.offT;
         g.z = p.z;
+        g.schunk = cyc_c_schunk(S.n, ctx->dev.num_sms);
         g.big_off = LC.big_off;
         g.bigset = LC.bigset;
         g.bigcnt = LC.bigcnt;

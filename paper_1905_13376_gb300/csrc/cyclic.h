@@ -41,6 +41,7 @@ struct CycCArgs {
     const uint2 *Tp;            // T grouped by F(c): (c, a)
     const uint32_t *offT;       // z + 1
     uint32_t z;
+    uint32_t schunk;            // S tuples of a work item at most (cyc_c_schunk)
     const unsigned long long *big_off;   // z + 1: big buckets' set regions (slots), scanned
     const unsigned long long *bigset;    // the regions: one slot per distinct (c, a) pair
     const uint32_t *bigcnt;              // the pairs' multiplicities, at the same indexes
@@ -54,6 +55,9 @@ struct CycCArgs {
 
 // T tuples a bucket's on-chip set holds (larger buckets keep theirs in the L2).
 uint32_t cyc_c_tcap();
+// S tuples of a work item at most: S_k is split so that a join with few
+// buckets (a small T) still gives every probe CTA work.
+uint32_t cyc_c_schunk(int64_t nS, int num_sms);
 // Slots of the probe CTAs' regions for chunks that repeat (c, a) pairs (the
 // rep_set (u64) and rep_cnt (u32) arguments of cyc_c_run).
 size_t cyc_c_rep_slots(int num_sms);

@@ -35,6 +35,7 @@ constexpr int RG_T = 512;                // threads of the grouping kernels
 constexpr uint32_t CC_QCAP = 2048;       // long R lists queued per work item
 constexpr uint32_t CC_CH = 256;          // wedges of a queued list per warp step
 constexpr uint32_t kQueueMin = 128;      // lists this long go to the item's queue
+constexpr uint32_t CC_SCHUNK_MIN = 32;   // S tuples of a bucket's work item, at least (a warp's batch)
 
 __device__ __forceinline__ unsigned long long cpack(uint32_t c, uint32_t a) {
     return ((unsigned long long)c << 32) | a;
@@ -182,15 +183,22 @@ __global__ void __launch_bounds__(RG_T) k_rg_scatter(const int32_t *__restrict__
 
 __host__ __device__ __forceinline__ bool cc_big(uint32_t nt) { return nt > kChunkMax * CC_TCAP; }
 
-// Work items of a bucket whose S_k and T_k are both non-empty: its on-chip
-// chunks, or one item when it is big (cc_big); a big bucket also gets a
+// S chunks of a bucket: S_k in pieces of at most schunk tuples
+__host__ __device__ __forceinline__ uint32_t cc_schunks(uint32_t ns, uint32_t schunk) {
+    return (ns + schunk - 1) / schunk;
+}
+
+// Work items of a bucket whose S_k and T_k are both non-empty: each of its
+// T chunks (on-chip sets; one set when the bucket is big, cc_big) with each
+// of its S chunks, item (t, s) at t * S chunks + s; a big bucket also gets a
 // region of 2^k >= 2 |T_k| slots for its set in the workspace (big_slots[k],
 // 0 for the others).
 __global__ void k_cc_plan(const uint32_t *__restrict__ offS, const uint32_t *__restrict__ offT, uint32_t z,
-                          uint32_t *__restrict__ items, unsigned long long *__restrict__ big_slots) {
+                          uint32_t schunk, uint32_t *__restrict__ items,
+                          unsigned long long *__restrict__ big_slots) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < z; k += gridDim.x * blockDim.x) {
         const uint32_t ns = offS[k + 1] - offS[k], nt = offT[k + 1] - offT[k];
-        items[k] = (ns && nt) ? (cc_big(nt) ? 1u : (nt + CC_TCAP - 1) / CC_TCAP) : 0u;
+        items[k] = (ns && nt) ? (cc_big(nt) ? 1u : (nt + CC_TCAP - 1) / CC_TCAP) * cc_schunks(ns, schunk) : 0u;
         unsigned long long slots = 0;
         if (ns && cc_big(nt)) {
             slots = 16;
@@ -303,11 +311,15 @@ __global__ void __launch_bounds__(CC_T, CC_MAX_CTAS_PER_SM) k_cc_probe(CycCArgs 
             if (item_off[mid] <= item) lo = mid; else hi = mid;
         }
         const uint32_t k = lo;
-        const uint32_t s0 = g.offS[k], s1 = g.offS[k + 1];
+        // (T chunk, S chunk) of this item
+        const uint32_t sch = cc_schunks(g.offS[k + 1] - g.offS[k], g.schunk);
+        const uint32_t li = item - item_off[k];
+        const uint32_t tci = li / sch, sci = li - tci * sch;
+        const uint32_t s0 = g.offS[k] + sci * g.schunk, s1 = min(g.offS[k + 1], s0 + g.schunk);
         // T_k's set: the item's chunk on chip, or for a big bucket its region
         // of the workspace, built before this kernel
         bool big = cc_big(g.offT[k + 1] - g.offT[k]);
-        const uint32_t ta = g.offT[k] + (item - item_off[k]) * CC_TCAP;
+        const uint32_t ta = g.offT[k] + tci * CC_TCAP;
         const uint32_t tz = big ? g.offT[k + 1] : min(g.offT[k + 1], ta + CC_TCAP);
         const unsigned long long gbase = g.big_off[k];
         uint32_t gmask = (uint32_t)(g.big_off[k + 1] - gbase) - 1u;
@@ -560,6 +572,15 @@ __global__ void k_cc_rows_check(const unsigned long long *base, uint32_t z, long
 
 }  // namespace
 
+uint32_t cyc_c_schunk(int64_t nS, int num_sms) {
+    // about four items per probe CTA over the whole of S: a join with few
+    // buckets (a small T, cheap to rebuild per item) is spread over the GPU,
+    // one with many buckets (S_k below the piece) is not split at all
+    const uint64_t want = ((uint64_t)(nS > 0 ? nS : 0) + 4ull * num_sms * CC_MAX_CTAS_PER_SM - 1) /
+                          (4ull * num_sms * CC_MAX_CTAS_PER_SM);
+    return (uint32_t)(want > CC_SCHUNK_MIN ? (want < 0x7FFFFFFFull ? want : 0x7FFFFFFFull) : CC_SCHUNK_MIN);
+}
+
 size_t cyc_c_rep_slots(int num_sms) { return (size_t)num_sms * CC_MAX_CTAS_PER_SM * CC_TSLOTS; }
 
 uint32_t cyc_c_tcap() { return CC_TCAP; }
@@ -601,7 +622,7 @@ cudaError_t cyc_c_run(const CycCArgs &g, uint32_t *items, void *scan_tmp, unsign
     cudaError_t e;
     {
         ProfScope ps_("cyc_c_plan", st);
-        k_cc_plan<<<(z + 255) / 256, 256, 0, st>>>(g.offS, g.offT, z, items, big_slots);
+        k_cc_plan<<<(z + 255) / 256, 256, 0, st>>>(g.offS, g.offT, z, g.schunk, items, big_slots);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(items + z, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;

@@ -138,6 +138,20 @@ def test_c_buckets_repeated_pairs(ctx, copies):
         check_all_modes(ctx, R, S, T, 40, shares=shares)
 
 
+def test_c_buckets_small_t_large_s(ctx):
+    """A small T (one or a few C buckets) and a large S: each bucket's S_k is
+    split into work items of its own (the bucket's set rebuilt for each), so
+    that the probe is spread over the GPU; every S chunk boundary, ragged
+    tail and shares (1, 1, z) give the oracle's result."""
+    g = np.random.default_rng(31)
+    nR, nS, nT = 5003, 300007, 517
+    R = (g.integers(0, 40, nR).astype(np.int32), g.integers(0, 50, nR).astype(np.int32))
+    S = (g.integers(0, 50, nS).astype(np.int32), g.integers(0, 60, nS).astype(np.int32))
+    T = (g.integers(0, 60, nT).astype(np.int32), g.integers(0, 40, nT).astype(np.int32))
+    for shares in [None, (1, 1, 2), (1, 1, 8)]:
+        check_all_modes(ctx, R, S, T, 40, shares=shares, rows=shares is None)
+
+
 def test_c_buckets_tiny_a_domain_zipf_c(ctx):
     """A large T over a tiny A domain with a Zipf C column: T's busiest C
     values repeat each (c, a) pair thousands of times, in big buckets' L2
