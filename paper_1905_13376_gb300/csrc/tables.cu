@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(BT, HLL_CTAS_PER_SM) k_hll(const int32_t *__re
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             if ((uint32_t)k >= cnt) break;
+            if (k > 0 && v[k] == v[k - 1]) continue;   // nothing a repeat could change
             kmin = min(kmin, v[k]);
             kmax = max(kmax, v[k]);
-            if (k > 0 && v[k] == v[k - 1]) continue;
             const uint32_t h = mix32((uint32_t)v[k] ^ seed);
             const uint32_t w = h << HLL_BITS;
             const uint32_t rank = (w == 0) ? (33u - HLL_BITS) : (uint32_t)__clz(w) + 1u;
